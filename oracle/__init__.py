@@ -1,0 +1,234 @@
+"""CPU oracle for the certificate-maintenance step (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this package.  It shares no code with the CUDA path: the brute-force
+core is plain C (``cert_oracle.c``), loaded with ctypes; the composition of a
+step and the selector network are plain numpy here and in ``mlp.py``.
+
+What each function follows in the paper ("Repair Entropy in Dynamic Geometric
+Nearest-Neighbour Structures"):
+
+* ``top2`` / ``top2_queries`` -- certificate (nn, d1^2, d2^2), Def. 1; exact
+  recomputation, Cor. A.2.  FP32, fixed operand order, lowest-index ties.
+* ``eps`` -- maximum step, Algorithm 1 (first statement).
+* ``frontier`` -- candidate frontier c_i <= 4 eps (+ rounding guard),
+  Algorithm 1 (second statement), Lemma 1.
+* ``grid_res`` / ``cells`` / ``entropy`` -- index cells, C and H(F_t), Def. 2.
+* ``step`` -- one maintenance step end to end (Algorithm 1 with every
+  certificate recomputed from scratch, which is the exact result Cor. A.2 says
+  the repair reaches), plus the failure audit of Table 1.
+* ``trunc_median`` -- the lower median truncated to 3 mantissa bits, the
+  definition the selector features use (no paper counterpart).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cert_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+CFLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+          "-fno-fast-math", "-fopenmp"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into ``oracle/liboracle.so`` (gcc, no FMA)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", *CFLAGS, "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        f32p = ctypes.POINTER(ctypes.c_float)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        L.oracle_top2.argtypes = [f32p, ctypes.c_int64, ctypes.c_int, i32p, f32p, f32p, ctypes.c_int]
+        L.oracle_top2.restype = ctypes.c_int
+        L.oracle_top2_queries.argtypes = [f32p, ctypes.c_int64, ctypes.c_int, i32p, ctypes.c_int64,
+                                          i32p, f32p, f32p, ctypes.c_int]
+        L.oracle_top2_queries.restype = ctypes.c_int
+        L.oracle_eps.argtypes = [f32p, f32p, ctypes.c_int64, ctypes.c_int]
+        L.oracle_eps.restype = ctypes.c_float
+        L.oracle_frontier.argtypes = [f32p, f32p, ctypes.c_int64, ctypes.c_float, ctypes.c_int, i32p]
+        L.oracle_frontier.restype = ctypes.c_int64
+        L.oracle_grid_res.argtypes = [ctypes.c_int64, ctypes.c_int]
+        L.oracle_grid_res.restype = ctypes.c_int
+        L.oracle_cells.argtypes = [f32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, i32p]
+        L.oracle_cells.restype = None
+        L.oracle_entropy.argtypes = [i32p, u8p, ctypes.c_int64, ctypes.c_int64, i64p, i64p]
+        L.oracle_entropy.restype = ctypes.c_double
+        L.oracle_max_threads.argtypes = []
+        L.oracle_max_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _pos(pos) -> np.ndarray:
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    if pos.ndim != 2 or pos.shape[1] not in (2, 3):
+        raise ValueError("positions must be [n][2] or [n][3] float32")
+    return pos
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())
+
+
+@dataclass
+class Certificates:
+    """(nn, d1^2, d2^2) of every point -- Def. 1 with squared distances."""
+    nn: np.ndarray
+    d1sq: np.ndarray
+    d2sq: np.ndarray
+
+
+def top2(pos, nthreads: int = 0) -> Certificates:
+    """Brute-force exact certificates of all points (Def. 1, Cor. A.2)."""
+    pos = _pos(pos)
+    n, dim = pos.shape
+    if n < 3:
+        raise ValueError("a certificate needs at least 3 points")
+    nn = np.empty(n, np.int32)
+    d1 = np.empty(n, np.float32)
+    d2 = np.empty(n, np.float32)
+    rc = lib().oracle_top2(_p(pos, ctypes.c_float), n, dim, _p(nn, ctypes.c_int32),
+                           _p(d1, ctypes.c_float), _p(d2, ctypes.c_float), int(nthreads))
+    assert rc == 0
+    return Certificates(nn, d1, d2)
+
+
+def top2_queries(pos, queries, nthreads: int = 0) -> Certificates:
+    """Certificates of a subset of query points against all points."""
+    pos = _pos(pos)
+    n, dim = pos.shape
+    q = np.ascontiguousarray(queries, dtype=np.int32)
+    nq = q.shape[0]
+    nn = np.empty(nq, np.int32)
+    d1 = np.empty(nq, np.float32)
+    d2 = np.empty(nq, np.float32)
+    rc = lib().oracle_top2_queries(_p(pos, ctypes.c_float), n, dim, _p(q, ctypes.c_int32), nq,
+                                   _p(nn, ctypes.c_int32), _p(d1, ctypes.c_float),
+                                   _p(d2, ctypes.c_float), int(nthreads))
+    if rc != 0:
+        raise ValueError("bad query list or point set")
+    return Certificates(nn, d1, d2)
+
+
+def eps(p_old, p_new) -> np.float32:
+    """Measured maximum step eps_t (Algorithm 1, first statement), FP32."""
+    a, b = _pos(p_old), _pos(p_new)
+    assert a.shape == b.shape
+    return np.float32(lib().oracle_eps(_p(a, ctypes.c_float), _p(b, ctypes.c_float),
+                                       a.shape[0], a.shape[1]))
+
+
+def frontier(d1sq, d2sq, eps_t, guard: bool = True) -> np.ndarray:
+    """Ascending candidate frontier {i : c_i <= 4 eps_t + tau_i} (Algorithm 1)."""
+    d1 = np.ascontiguousarray(d1sq, dtype=np.float32)
+    d2 = np.ascontiguousarray(d2sq, dtype=np.float32)
+    out = np.empty(d1.shape[0], np.int32)
+    k = lib().oracle_frontier(_p(d1, ctypes.c_float), _p(d2, ctypes.c_float), d1.shape[0],
+                              float(eps_t), 1 if guard else 0, _p(out, ctypes.c_int32))
+    return out[:k].copy()
+
+
+def grid_res(n: int, dim: int) -> int:
+    """Entropy-grid cells per axis: smallest g with g^dim >= n (Sec. 2)."""
+    return int(lib().oracle_grid_res(int(n), int(dim)))
+
+
+def cells(pos, g: int) -> np.ndarray:
+    """Index cell of every point under the g^dim entropy grid (Def. 2)."""
+    pos = _pos(pos)
+    out = np.empty(pos.shape[0], np.int32)
+    lib().oracle_cells(_p(pos, ctypes.c_float), pos.shape[0], pos.shape[1], int(g),
+                       _p(out, ctypes.c_int32))
+    return out
+
+
+def entropy(cell, member, ncells: int):
+    """(H, m, C): normalised entropy of ``member`` over the occupied cells (Def. 2)."""
+    cell = np.ascontiguousarray(cell, dtype=np.int32)
+    mem = np.ascontiguousarray(member, dtype=np.uint8)
+    m = ctypes.c_int64(0)
+    C = ctypes.c_int64(0)
+    H = lib().oracle_entropy(_p(cell, ctypes.c_int32), _p(mem, ctypes.c_uint8), cell.shape[0],
+                             int(ncells), ctypes.byref(m), ctypes.byref(C))
+    return float(H), int(m.value), int(C.value)
+
+
+def trunc_median(values) -> np.float32:
+    """Lower median (rank floor((n-1)/2)) of non-negative FP32 values, truncated
+    to its sign, exponent and top 3 mantissa bits (bit pattern & 0xFFF00000).
+    This is the exact definition behind the selector's median features."""
+    v = np.sort(np.ascontiguousarray(values, dtype=np.float32))
+    med = v[(v.shape[0] - 1) // 2]
+    bits = np.array([med], np.float32).view(np.uint32) & np.uint32(0xFFF00000)
+    return bits.view(np.float32)[0]
+
+
+@dataclass
+class StepResult:
+    """Everything one maintenance step reports, per the paper's audit columns."""
+    eps_t: np.float32
+    frontier: np.ndarray          # ascending indices (detected set)
+    cert: Certificates            # post-step certificates (exact)
+    failed: np.ndarray            # bool: nn changed across the step (true failures)
+    cell: np.ndarray              # post-step entropy-grid cell of every point
+    g_h: int
+    H: float                      # entropy of the true failures (Def. 2)
+    H_cand: float                 # entropy of the detected frontier
+    m: int                        # cells the failures meet
+    m_cand: int                   # cells the detected frontier meets
+    C: int                        # occupied cells
+    n_failed: int
+    n_missed: int                 # failed but not detected (Lemma 1: must be 0)
+    n_false: int                  # detected but not failed
+    med_c: np.float32             # trunc_median of the pre-step clearances
+
+
+def clearances(cert: Certificates) -> np.ndarray:
+    """c_i = d2_i - d1_i in FP32 with d_k = sqrtf(d_k^2) (Def. 1)."""
+    return (np.sqrt(cert.d2sq) - np.sqrt(cert.d1sq)).astype(np.float32)
+
+
+def step(p_old, p_new, cert_old: Certificates, nthreads: int = 0) -> StepResult:
+    """One maintenance step: eps_t, the detected frontier from the pre-step
+    certificates, exact post-step certificates, true failures, cells, H and the
+    audit (Algorithm 1; Def. 2; Cor. A.2; Table 1 columns)."""
+    p_old, p_new = _pos(p_old), _pos(p_new)
+    n, dim = p_new.shape
+    e = eps(p_old, p_new)
+    F = frontier(cert_old.d1sq, cert_old.d2sq, e)
+    new = top2(p_new, nthreads)
+    failed = new.nn != cert_old.nn
+    g = grid_res(n, dim)
+    cell = cells(p_new, g)
+    inF = np.zeros(n, bool)
+    inF[F] = True
+    H, m, C = entropy(cell, failed, g ** dim)
+    Hc, mc, _ = entropy(cell, inF, g ** dim)
+    return StepResult(
+        eps_t=e, frontier=F, cert=new, failed=failed, cell=cell, g_h=g, H=H, H_cand=Hc,
+        m=m, m_cand=mc, C=C, n_failed=int(failed.sum()),
+        n_missed=int((failed & ~inF).sum()), n_false=int((inF & ~failed).sum()),
+        med_c=trunc_median(clearances(cert_old)))
