@@ -1,0 +1,187 @@
+/*
+ * cert.h -- C ABI of libcert.so: exact nearest-neighbour certificates for
+ * points moving by small steps in 2-D and 3-D, maintained on one B300 GPU.
+ *
+ * Paper: "Repair Entropy in Dynamic Geometric Nearest-Neighbour Structures".
+ *   certificate (nn_i, d1_i, d2_i), clearance c_i = d2_i - d1_i  ...... Sec. 2, Def. 1
+ *   safety rule: c_i > 4 eps  =>  nn_i unchanged ..................... Lemma 1, Thm A.1
+ *   one maintenance step (eps, frontier, cell update, block repair) .. Algorithm 1
+ *   frontier entropy H(F_t) over the occupied index cells ............. Def. 2
+ *   exactness of the widened-block repair ............................. Cor. A.2
+ *   incremental repair vs rebuild vs exact all-pairs pass ............. Sec. 3 (strategies)
+ *
+ * Conventions (every entry point):
+ *   - Positions are float32, contiguous [n][dim] (dim = 2 or 3), in DEVICE
+ *     memory owned by the caller, unless the name ends in _host.  They are
+ *     expected in the unit domain [0,1]^dim; points outside are clamped into
+ *     the boundary index cells, which keeps every result exact.
+ *   - Squared distances use the fixed FP32 order ((dx*dx + dy*dy) + dz*dz),
+ *     dx = x_j - x_i, each operation rounded to nearest, no FMA.  Equal
+ *     squared distances are ordered by the lower point index.
+ *   - Indices in results are scene-local (0 .. n_s - 1).
+ *   - A stream argument is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Entry points that take a stream only enqueue work and
+ *     never synchronise, unless documented otherwise.
+ *   - Errors: host-detectable argument errors return immediately, nothing is
+ *     enqueued.  Device-side conditions (a bounded wait that gave up, a
+ *     non-finite coordinate, eps_t above the declared eps) are latched in a
+ *     device status word and reported by cert_sync_result.  No entry point
+ *     throws, aborts or prints.
+ *   - Thread safety: one context must not be used from two threads at once.
+ */
+#ifndef CERT_H
+#define CERT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cert_ctx cert_ctx;
+
+typedef enum {
+    CERT_OK = 0,
+    CERT_EINVAL = 1,   /* bad argument; or (latched) a non-finite coordinate      */
+    CERT_ENOMEM = 2,   /* device allocation failed                                 */
+    CERT_ECUDA = 3,    /* a CUDA runtime call failed; see cert_last_error          */
+    CERT_ETIMEOUT = 4, /* (latched) a bounded device-side wait gave up             */
+    CERT_EBOUND = 5,   /* (latched, warning) measured eps_t > declared eps         */
+    CERT_ESTATE = 6    /* call not valid in the context's current state            */
+} cert_status;
+
+typedef enum {
+    CERT_AUTO = 0,        /* per scene: the loaded selector's choice, else the policy */
+    CERT_INCREMENTAL = 1, /* refresh safe certificates, grid-repair frontier (Alg. 1) */
+    CERT_REBUILD = 2,     /* grid search for every point (O(N) rebuild)               */
+    CERT_ALLPAIRS = 3     /* exact all-pairs pass for every point (O(N^2))            */
+} cert_strategy;
+
+/* Batch description.  One context holds n_scenes independent scenes whose
+ * points are concatenated in scene order: scene s owns points
+ * offsets[s] .. offsets[s+1]-1 of every position / result array. */
+typedef struct {
+    int32_t dim;              /* 2 or 3                                               */
+    int32_t n_scenes;         /* >= 1                                                 */
+    const int64_t *offsets;   /* HOST array [n_scenes+1]; offsets[0] = 0, strictly
+                                 increasing, every scene >= 3 points, total < 2^31;
+                                 NULL allowed when n_scenes == 1 together with n_total */
+    int64_t n_total;          /* total points (used when offsets == NULL)             */
+    float cell_scale;         /* search-grid cell side / median d2 (0 -> 1.5)         */
+    int32_t policy;           /* strategy for CERT_AUTO without a selector (0 -> INCREMENTAL) */
+    int32_t reserved[4];      /* must be zero                                          */
+} cert_config;
+
+/* Per-scene scalars of the last step.  Same layout on device and host. */
+typedef struct {
+    double H;                 /* entropy of the true failures over the entropy grid, Def. 2 */
+    double H_cand;            /* entropy of the detected frontier F_t                         */
+    float eps_t;              /* measured max_i ||p'_i - p_i||, Algorithm 1                   */
+    float med_c;              /* lower median of the pre-step clearances over the first
+                                 min(n,1024) points, truncated to 3 mantissa bits            */
+    int32_t n_frontier;       /* |F_t| = #{i : c_i <= 4 eps_t + tau_i} (pre-step certificates) */
+    int32_t frontier_start;   /* offset of this scene's frontier list in the frontier array  */
+    int32_t n_failed;         /* #{i : nn_i changed across the step}                          */
+    int32_t n_missed;         /* failed but not in F_t (Lemma 1: always 0)                    */
+    int32_t n_false;          /* in F_t but not failed                                         */
+    int32_t n_searched;       /* certificates recomputed by a search this step                */
+    int32_t failed_cells;     /* m: entropy-grid cells the failures meet (Thm A.4)            */
+    int32_t frontier_cells;   /* cells the detected frontier meets                             */
+    int32_t occupied_cells;   /* C: cells holding at least one point                           */
+    int32_t strategy;         /* cert_strategy applied to this scene                           */
+    float pred_inc;           /* selector output: predicted ln step time, incremental (0 if none) */
+    float pred_reb;           /* selector output: predicted ln step time, rebuild               */
+    int32_t grid_res;         /* entropy-grid cells per axis (smallest g with g^dim >= n)      */
+    int32_t search_res;       /* search-grid cells per axis used this step                      */
+} cert_scene_result;
+
+/* Device views of the per-point results; valid until the next call that
+ * modifies the context.  All arrays are [n_total] unless noted. */
+typedef struct {
+    const int32_t *nn;        /* nearest neighbour (scene-local index)                        */
+    const float *d1sq;        /* squared distance to nn                                       */
+    const float *d2sq;        /* squared distance to the runner-up                            */
+    const int32_t *cell;      /* entropy-grid cell of the post-step position (scene-local)   */
+    const int32_t *frontier;  /* ascending frontier lists, scene s at [frontier_start, +n_frontier) */
+    const uint8_t *failed;    /* 1 where nn changed across the last step                      */
+    const cert_scene_result *scenes; /* [n_scenes] device copy of the scalars                */
+    int64_t n_total;
+    int32_t n_scenes;
+    int32_t dim;
+} cert_views;
+
+/* Create a context and compute the initial certificates of d_pos by a full
+ * grid search (exact; Def. 1).  d_pos: device [n_total][dim] float32.
+ * Allocates every device buffer the context will use; later calls on the
+ * context allocate nothing.  On error *out is NULL. */
+cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos, void *stream);
+
+/* One maintenance step to positions d_pos_new (Algorithm 1, with every
+ * certificate exact afterwards, Cor. A.2): eps_t, the ascending frontier from
+ * the pre-step certificates, the index rebuild, the chosen strategy's repair,
+ * failure marks, H(F_t) and the audit.  eps is the declared step bound (>= 0,
+ * finite): the rule always uses the measured eps_t; eps_t > eps*(1+2^-20) only
+ * latches CERT_EBOUND.  strategy: cert_strategy.  Stream-ordered, no host
+ * synchronisation, no allocation, capturable in a CUDA graph.  out may be NULL. */
+cert_status cert_step(cert_ctx *ctx, const float *d_pos_new, float eps, int32_t strategy,
+                      cert_views *out, void *stream);
+
+/* The same step with HOST buffers: copies h_pos_new (pinned for full speed)
+ * to the device, runs cert_step, copies the per-scene scalars into
+ * h_scenes[n_scenes] and synchronises the stream before returning. */
+cert_status cert_step_host(cert_ctx *ctx, const float *h_pos_new, float eps, int32_t strategy,
+                           cert_scene_result *h_scenes, void *stream);
+
+/* Recompute every certificate of the current positions by a full grid search
+ * (the O(N) rebuild of Sec. 3).  Step outputs (frontier, failures, H) keep the
+ * values of the last step. */
+cert_status cert_rebuild(cert_ctx *ctx, void *stream);
+
+/* Views of the current results (no device work). */
+cert_status cert_get_views(const cert_ctx *ctx, cert_views *out);
+
+/* Wait for the context's last stream, copy the per-scene scalars to
+ * h_scenes[n_scenes] (may be NULL), and return the latched device status
+ * (CERT_OK, CERT_EBOUND, CERT_ETIMEOUT or CERT_EINVAL), clearing it. */
+cert_status cert_sync_result(cert_ctx *ctx, cert_scene_result *h_scenes);
+
+/* d1 = sqrtf(d1^2), d2 = sqrtf(d2^2) of every current certificate (correctly
+ * rounded), written to caller device buffers [n_total]. */
+cert_status cert_distances(cert_ctx *ctx, float *d_d1, float *d_d2, void *stream);
+
+/* Exact all-pairs certificates (the paper's brute-force oracle pass, Sec. 3,
+ * Table 2) of a single point set d_pos [n][dim] (n >= 3): for each query --
+ * every point when d_queries is NULL, else the nq listed indices -- the top-2
+ * over all j != query.  Outputs are caller device buffers of length n (or nq).
+ * Uses library-managed scratch from the stream-ordered allocator. */
+cert_status cert_allpairs(const float *d_pos, int64_t n, int32_t dim, const int32_t *d_queries,
+                          int64_t nq, int32_t *d_nn, float *d_d1sq, float *d_d2sq, void *stream);
+
+/* Number of timed phases per step (see cert_profile_end). */
+#define CERT_N_PHASES 7
+
+/* Diagnostics: while enabled, cert_step records a CUDA event on its stream
+ * before the first and after every phase of the next max_steps steps
+ * (phases: 0 clear accumulators, 1 prepare, 2 scans, 3 select, 4 scatter and
+ * refresh -- or all-pairs tiles, 5 grid search -- or all-pairs merge,
+ * 6 finalize).  Creates the events here, so the timed steps allocate nothing. */
+cert_status cert_profile_begin(cert_ctx *ctx, int32_t max_steps);
+
+/* Stop recording, wait for the recorded steps and write h_ms[step][phase]
+ * (milliseconds, CERT_N_PHASES per step) for *n_steps <= max_steps steps. */
+cert_status cert_profile_end(cert_ctx *ctx, float *h_ms, int32_t max_steps, int32_t *n_steps);
+
+/* Release every resource of the context (synchronises it first). */
+void cert_destroy(cert_ctx *ctx);
+
+/* Text of the last error on this context (ctx == NULL: of the calling thread). */
+const char *cert_last_error(const cert_ctx *ctx);
+
+/* Library version string. */
+const char *cert_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CERT_H */

@@ -176,11 +176,16 @@ def entropy(cell, member, ncells: int):
     return float(H), int(m.value), int(C.value)
 
 
+MEDIAN_SAMPLE = 1024
+
+
 def trunc_median(values) -> np.float32:
-    """Lower median (rank floor((n-1)/2)) of non-negative FP32 values, truncated
-    to its sign, exponent and top 3 mantissa bits (bit pattern & 0xFFF00000).
-    This is the exact definition behind the selector's median features."""
-    v = np.sort(np.ascontiguousarray(values, dtype=np.float32))
+    """Lower median (rank floor((k-1)/2)) of the first k = min(n, 1024)
+    non-negative FP32 values, truncated to its sign, exponent and top 3
+    mantissa bits (bit pattern & 0xFFF00000).  This is the exact definition
+    behind the selector's median features (a fixed sample keeps it O(1) per
+    scene); it has no counterpart in the paper."""
+    v = np.sort(np.ascontiguousarray(values, dtype=np.float32)[:MEDIAN_SAMPLE])
     med = v[(v.shape[0] - 1) // 2]
     bits = np.array([med], np.float32).view(np.uint32) & np.uint32(0xFFF00000)
     return bits.view(np.float32)[0]

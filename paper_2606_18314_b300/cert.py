@@ -1,0 +1,296 @@
+"""Thin ctypes binding of libcert.so (include/cert.h).  Argument marshalling only:
+every step of the certificate loop runs in the library's CUDA kernels.
+
+Device buffers are torch CUDA tensors (torch is used for device memory and
+streams only); results come back as zero-copy torch views of the library's
+device arrays.  The library must have been built in-tree
+(``python -m paper_2606_18314_b300.build``); loading fails loudly otherwise --
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcert.so")
+
+CERT_OK, CERT_EINVAL, CERT_ENOMEM, CERT_ECUDA, CERT_ETIMEOUT, CERT_EBOUND, CERT_ESTATE = range(7)
+STATUS_NAMES = ["CERT_OK", "CERT_EINVAL", "CERT_ENOMEM", "CERT_ECUDA", "CERT_ETIMEOUT", "CERT_EBOUND",
+                "CERT_ESTATE"]
+CERT_AUTO, CERT_INCREMENTAL, CERT_REBUILD, CERT_ALLPAIRS = range(4)
+STRATEGY = {"auto": CERT_AUTO, "incremental": CERT_INCREMENTAL, "rebuild": CERT_REBUILD,
+            "allpairs": CERT_ALLPAIRS}
+
+
+class cert_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n_scenes", ctypes.c_int32),
+                ("offsets", ctypes.POINTER(ctypes.c_int64)), ("n_total", ctypes.c_int64),
+                ("cell_scale", ctypes.c_float), ("policy", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class cert_scene_result(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_double), ("H_cand", ctypes.c_double), ("eps_t", ctypes.c_float),
+                ("med_c", ctypes.c_float), ("n_frontier", ctypes.c_int32),
+                ("frontier_start", ctypes.c_int32), ("n_failed", ctypes.c_int32),
+                ("n_missed", ctypes.c_int32), ("n_false", ctypes.c_int32),
+                ("n_searched", ctypes.c_int32), ("failed_cells", ctypes.c_int32),
+                ("frontier_cells", ctypes.c_int32), ("occupied_cells", ctypes.c_int32),
+                ("strategy", ctypes.c_int32), ("pred_inc", ctypes.c_float), ("pred_reb", ctypes.c_float),
+                ("grid_res", ctypes.c_int32), ("search_res", ctypes.c_int32)]
+
+
+SCENE_DTYPE = np.dtype([(n, np.dtype(t).newbyteorder("=")) for n, t in [
+    ("H", np.float64), ("H_cand", np.float64), ("eps_t", np.float32), ("med_c", np.float32),
+    ("n_frontier", np.int32), ("frontier_start", np.int32), ("n_failed", np.int32),
+    ("n_missed", np.int32), ("n_false", np.int32), ("n_searched", np.int32),
+    ("failed_cells", np.int32), ("frontier_cells", np.int32), ("occupied_cells", np.int32),
+    ("strategy", np.int32), ("pred_inc", np.float32), ("pred_reb", np.float32),
+    ("grid_res", np.int32), ("search_res", np.int32)]])
+assert SCENE_DTYPE.itemsize == ctypes.sizeof(cert_scene_result)
+
+
+class cert_views(ctypes.Structure):
+    _fields_ = [("nn", ctypes.c_void_p), ("d1sq", ctypes.c_void_p), ("d2sq", ctypes.c_void_p),
+                ("cell", ctypes.c_void_p), ("frontier", ctypes.c_void_p), ("failed", ctypes.c_void_p),
+                ("scenes", ctypes.c_void_p), ("n_total", ctypes.c_int64), ("n_scenes", ctypes.c_int32),
+                ("dim", ctypes.c_int32)]
+
+
+_lib = None
+
+# every symbol include/cert.h declares (checked by the CPU tests)
+EXPORTS = ["cert_init", "cert_step", "cert_step_host", "cert_rebuild", "cert_get_views",
+           "cert_sync_result", "cert_distances", "cert_allpairs", "cert_destroy", "cert_last_error",
+           "cert_version", "cert_profile_begin", "cert_profile_end"]
+N_PHASES = 7
+PHASE_NAMES = ["clear", "prepare", "scan", "select", "scatter_refresh", "search", "finalize"]
+
+
+def lib():
+    """Load libcert.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libcert.so not built ({LIB_PATH}); run python -m paper_2606_18314_b300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    L.cert_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(cert_config), vp, vp]
+    L.cert_step.argtypes = [vp, vp, f32, i32, ctypes.POINTER(cert_views), vp]
+    L.cert_step_host.argtypes = [vp, vp, f32, i32, vp, vp]
+    L.cert_rebuild.argtypes = [vp, vp]
+    L.cert_get_views.argtypes = [vp, ctypes.POINTER(cert_views)]
+    L.cert_sync_result.argtypes = [vp, vp]
+    L.cert_distances.argtypes = [vp, vp, vp, vp]
+    L.cert_allpairs.argtypes = [vp, i64, i32, vp, i64, vp, vp, vp, vp]
+    L.cert_destroy.argtypes = [vp]
+    L.cert_destroy.restype = None
+    L.cert_last_error.argtypes = [vp]
+    L.cert_last_error.restype = ctypes.c_char_p
+    L.cert_version.argtypes = []
+    L.cert_version.restype = ctypes.c_char_p
+    L.cert_profile_begin.argtypes = [vp, i32]
+    L.cert_profile_end.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+    for name in ["cert_init", "cert_step", "cert_step_host", "cert_rebuild", "cert_get_views",
+                 "cert_sync_result", "cert_distances", "cert_allpairs", "cert_profile_begin",
+                 "cert_profile_end"]:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class CertError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else code}: {msg}")
+        self.code = code
+
+
+def _check(code, ctx=None):
+    if code != CERT_OK:
+        msg = lib().cert_last_error(ctx).decode(errors="replace")
+        raise CertError(code, msg)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype_name, shape_last=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    if str(t.dtype) != dtype_name:
+        raise TypeError(f"expected {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if shape_last is not None and (t.dim() != 2 or t.shape[1] != shape_last):
+        raise ValueError(f"expected shape [n][{shape_last}]")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _CudaArray:
+    """__cuda_array_interface__ wrapper so torch can view a library buffer."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape),
+                                         "typestr": typestr, "version": 3, "strides": None}
+        self._owner = owner
+
+
+def _view(ptr, shape, typestr, owner):
+    import torch
+    if any(s == 0 for s in shape):
+        return torch.empty(shape, dtype={"<i4": torch.int32, "<f4": torch.float32, "|u1": torch.uint8}[typestr],
+                           device="cuda")
+    return torch.as_tensor(_CudaArray(ptr, shape, typestr, owner), device="cuda")
+
+
+def cert_version() -> str:
+    return lib().cert_version().decode()
+
+
+def cert_last_error(ctx=None) -> str:
+    return lib().cert_last_error(ctx).decode(errors="replace")
+
+
+def cert_allpairs(pos, queries=None, stream=None):
+    """Exact top-2 of every point (or of the listed query indices) against all
+    points of one set: returns (nn, d1sq, d2sq) as CUDA tensors."""
+    import torch
+    dim = pos.shape[1]
+    pp = _dev_ptr(pos, "torch.float32", dim)
+    n = pos.shape[0]
+    if queries is not None:
+        qp = _dev_ptr(queries, "torch.int32")
+        nq = queries.shape[0]
+    else:
+        qp, nq = None, n
+    nn = torch.empty(nq, dtype=torch.int32, device=pos.device)
+    d1 = torch.empty(nq, dtype=torch.float32, device=pos.device)
+    d2 = torch.empty(nq, dtype=torch.float32, device=pos.device)
+    _check(lib().cert_allpairs(pp, n, dim, qp, nq, ctypes.c_void_p(nn.data_ptr()),
+                               ctypes.c_void_p(d1.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
+                               _stream_ptr(stream)))
+    return nn, d1, d2
+
+
+class Context:
+    """A batch of scenes whose certificates are maintained on the GPU.
+
+    ``Context(pos, offsets=None)`` calls ``cert_init``; ``step`` calls
+    ``cert_step``; ``views`` exposes the per-point results as torch tensors
+    (valid until the next call); ``sync`` calls ``cert_sync_result``.
+    """
+
+    def __init__(self, pos, offsets=None, cell_scale=0.0, policy=CERT_INCREMENTAL, stream=None):
+        import torch
+        self.dim = int(pos.shape[1])
+        self._keep = []
+        cfg = cert_config()
+        cfg.dim = self.dim
+        if offsets is None:
+            offsets = np.array([0, pos.shape[0]], np.int64)
+        offsets = np.ascontiguousarray(offsets, np.int64)
+        self.offsets = offsets
+        cfg.n_scenes = len(offsets) - 1
+        cfg.offsets = offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        cfg.n_total = int(offsets[-1])
+        cfg.cell_scale = float(cell_scale)
+        cfg.policy = int(policy)
+        self.n_scenes = cfg.n_scenes
+        self.n = cfg.n_total
+        h = ctypes.c_void_p()
+        if pos.shape[0] != cfg.n_total:
+            raise ValueError("positions do not match the offsets")
+        _check(lib().cert_init(ctypes.byref(h), ctypes.byref(cfg), _dev_ptr(pos, "torch.float32", self.dim),
+                               _stream_ptr(stream)))
+        self.h = h
+        self.device = pos.device
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cert_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, pos_new, eps, strategy=CERT_INCREMENTAL, stream=None):
+        if isinstance(strategy, str):
+            strategy = STRATEGY[strategy]
+        if pos_new.shape[0] != self.n:
+            raise ValueError("positions do not match the context's point count")
+        _check(lib().cert_step(self.h, _dev_ptr(pos_new, "torch.float32", self.dim), float(eps),
+                               int(strategy), None, _stream_ptr(stream)), self.h)
+
+    def step_host(self, pos_new_host: np.ndarray, eps, strategy=CERT_INCREMENTAL, stream=None):
+        """cert_step_host: host positions in, per-scene scalars out (synchronous)."""
+        if isinstance(strategy, str):
+            strategy = STRATEGY[strategy]
+        out = np.zeros(self.n_scenes, SCENE_DTYPE)
+        a = pos_new_host
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous
+                and a.shape == (self.n, self.dim)):
+            raise ValueError("host positions must be C-contiguous float32 [n][dim]")
+        _check(lib().cert_step_host(self.h, ctypes.c_void_p(a.ctypes.data), float(eps), int(strategy),
+                                    ctypes.c_void_p(out.ctypes.data), _stream_ptr(stream)), self.h)
+        return out
+
+    def step_host_ptr(self, host_ptr: int, eps, strategy, out: np.ndarray, stream=None):
+        """cert_step_host on a raw (pinned) host pointer; ``out`` receives the scalars."""
+        _check(lib().cert_step_host(self.h, ctypes.c_void_p(host_ptr), float(eps), int(strategy),
+                                    ctypes.c_void_p(out.ctypes.data), _stream_ptr(stream)), self.h)
+
+    def rebuild(self, stream=None):
+        _check(lib().cert_rebuild(self.h, _stream_ptr(stream)), self.h)
+
+    def views(self):
+        v = cert_views()
+        _check(lib().cert_get_views(self.h, ctypes.byref(v)), self.h)
+        n = int(v.n_total)
+        return {
+            "nn": _view(v.nn, (n,), "<i4", self),
+            "d1sq": _view(v.d1sq, (n,), "<f4", self),
+            "d2sq": _view(v.d2sq, (n,), "<f4", self),
+            "cell": _view(v.cell, (n,), "<i4", self),
+            "frontier": _view(v.frontier, (n,), "<i4", self),
+            "failed": _view(v.failed, (n,), "|u1", self),
+        }
+
+    def sync(self, raise_on_status=True):
+        """cert_sync_result: per-scene scalars as a numpy structured array."""
+        out = np.zeros(self.n_scenes, SCENE_DTYPE)
+        rc = lib().cert_sync_result(self.h, ctypes.c_void_p(out.ctypes.data))
+        if raise_on_status:
+            _check(rc, self.h)
+        return out, rc
+
+    def distances(self, stream=None):
+        import torch
+        d1 = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        d2 = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        _check(lib().cert_distances(self.h, ctypes.c_void_p(d1.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
+                                    _stream_ptr(stream)), self.h)
+        return d1, d2
+
+    def profile_begin(self, max_steps):
+        _check(lib().cert_profile_begin(self.h, int(max_steps)), self.h)
+        self._prof_max = int(max_steps)
+
+    def profile_end(self):
+        """Per-step phase times in ms, shape [steps][N_PHASES]."""
+        mx = getattr(self, "_prof_max", 0)
+        out = np.zeros((max(mx, 1), N_PHASES), np.float32)
+        n = ctypes.c_int32(0)
+        _check(lib().cert_profile_end(self.h, ctypes.c_void_p(out.ctypes.data), mx, ctypes.byref(n)), self.h)
+        return out[:n.value]

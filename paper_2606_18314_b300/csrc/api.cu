@@ -1,0 +1,611 @@
+// api.cu -- host implementation of the C ABI declared in include/cert.h.
+//
+// A context owns one device allocation carved into every buffer a batch of
+// scenes needs; cert_init sizes it from the scene offsets and nothing is
+// allocated afterwards (cert_allpairs, which has no context, uses the
+// stream-ordered allocator).  Every call only enqueues work on the caller's
+// stream, except cert_sync_result / cert_step_host / cert_destroy, which wait.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cert_internal.cuh"
+#include "cert_launch.h"
+
+using namespace certk;
+
+struct cert_ctx {
+    int dim = 0, S = 0;
+    int64_t N = 0;
+    float cell_scale = 1.5f;
+    int policy = STRAT_INC;
+    std::vector<SceneParams> h_sp;
+    int n_buckets = 0, n_buckets_pad = 0, ntiles_b = 0, ntiles_p = 0;
+    int64_t n_h = 0, ap_P = 0;
+    int n_ap_items = 0;
+    char *blob = nullptr;
+    size_t blob_bytes = 0;
+    // persistent buffers
+    SceneParams *sp = nullptr;
+    SceneState *st = nullptr;
+    cert_scene_result *res = nullptr;
+    uint32_t *status = nullptr;
+    int32_t *fstart = nullptr, *scene_of = nullptr;
+    float4 *pos[2] = {nullptr, nullptr};
+    int cur = 0;
+    int32_t *nn = nullptr, *nn2 = nullptr;
+    float *d1sq = nullptr, *d2sq = nullptr, *L = nullptr;
+    int32_t *hcell = nullptr, *frontier = nullptr;
+    uint8_t *inF = nullptr, *failed = nullptr, *sflag = nullptr;
+    int2 *brank = nullptr;
+    float4 *sorted = nullptr;
+    int32_t *bucket_start = nullptr;
+    double *nlogn = nullptr;
+    float *stage = nullptr;
+    APItem *ap_items = nullptr;
+    float *ap_pd = nullptr;
+    int32_t *ap_pj = nullptr;
+    float *sel_params = nullptr, *sel_norm = nullptr;
+    bool have_sel = false;
+    // zeroed at the start of every call that runs the pipeline
+    char *zero = nullptr;
+    size_t zero_bytes = 0;
+    SceneAcc *acc = nullptr;
+    uint32_t *tile_ctr = nullptr;
+    uint64_t *tstat_b = nullptr, *tstat_p = nullptr;
+    int32_t *bucket_count = nullptr, *hocc = nullptr, *hfail = nullptr, *hcand = nullptr;
+    cudaStream_t last = nullptr;
+    bool stepped = false;
+    // phase profiling (diagnostics)
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_max = 0, prof_n = 0;
+    bool prof_on = false;
+    std::string err;
+};
+
+static thread_local std::string g_err;
+
+static cert_status fail(cert_ctx *ctx, cert_status code, const std::string &msg)
+{
+    if (ctx)
+        ctx->err = msg;
+    g_err = msg;
+    return code;
+}
+
+static cert_status cuda_fail(cert_ctx *ctx, const char *what, cudaError_t e)
+{
+    return fail(ctx, CERT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                               \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), #call, e_);  \
+    } while (0)
+
+static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static int next_pow2(int64_t v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+static int entropy_res(int64_t n, int dim)
+{
+    int g = 1;
+    for (;;) {
+        int64_t p = 1;
+        for (int a = 0; a < dim; ++a) p *= g;
+        if (p >= n) return g;
+        ++g;
+    }
+}
+
+// Bump allocator over one device allocation (256-byte aligned pieces).
+struct Carver {
+    size_t off = 0;
+    template <typename T>
+    size_t take(int64_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        const size_t at = off;
+        off += size_t(count) * sizeof(T);
+        return at;
+    }
+};
+
+static StepArgs make_args(cert_ctx *c, int mode)
+{
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.mode = mode;
+    a.dim = c->dim;
+    a.n_total = (int)c->N;
+    a.n_scenes = c->S;
+    a.scene_of = c->scene_of;
+    a.sp = c->sp;
+    a.st = c->st;
+    a.acc = c->acc;
+    a.status = c->status;
+    a.bucket_count = c->bucket_count;
+    a.bucket_start = c->bucket_start;
+    a.brank = c->brank;
+    a.sorted = c->sorted;
+    a.sflag = c->sflag;
+    a.nn = c->nn;
+    a.nn2 = c->nn2;
+    a.d1sq = c->d1sq;
+    a.d2sq = c->d2sq;
+    a.L = c->L;
+    a.hcell = c->hcell;
+    a.hocc = c->hocc;
+    a.hfail = c->hfail;
+    a.hcand = c->hcand;
+    a.inF = c->inF;
+    a.failed = c->failed;
+    a.frontier = c->frontier;
+    a.fstart = c->fstart;
+    a.tstat_b = c->tstat_b;
+    a.tstat_p = c->tstat_p;
+    a.tile_ctr = c->tile_ctr;
+    a.ntiles_b = c->ntiles_b;
+    a.ntiles_p = 0;
+    a.nlogn = c->nlogn;
+    a.res = c->res;
+    a.policy = c->policy;
+    a.cell_scale = c->cell_scale;
+    a.sel_params = c->have_sel ? c->sel_params : nullptr;
+    a.sel_norm = c->sel_norm;
+    return a;
+}
+
+// Grid build + full search of every point of the current positions
+// (initial certificates and cert_rebuild).
+static cert_status run_full(cert_ctx *c, int mode, const float *pos_in, cudaStream_t s)
+{
+    StepArgs a = make_args(c, mode);
+    a.pos_in = pos_in;
+    a.pos_new = c->pos[c->cur];
+    CK(c, cudaMemsetAsync(c->zero, 0, c->zero_bytes, s));
+    CK(c, launch_step_phase(a, PH_PREPARE, s));
+    CK(c, launch_step_phase(a, PH_SCAN, s));
+    CK(c, launch_step_phase(a, PH_SCATTER, s));
+    CK(c, launch_step_phase(a, PH_SEARCH, s));
+    CK(c, launch_step_phase(a, PH_SELECT, s));
+    CK(c, launch_step_phase(a, PH_FINALIZE, s));
+    c->last = s;
+    return CERT_OK;
+}
+
+extern "C" {
+
+const char *cert_version(void) { return "certmaint-b300 0.1 (sm_103a)"; }
+
+const char *cert_last_error(const cert_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos, void *stream)
+{
+    if (!out) return fail(nullptr, CERT_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, CERT_EINVAL, "cfg is NULL");
+    if (!d_pos) return fail(nullptr, CERT_EINVAL, "positions are NULL");
+    if (cfg->dim != 2 && cfg->dim != 3) return fail(nullptr, CERT_EINVAL, "dim must be 2 or 3");
+    if (cfg->n_scenes < 1) return fail(nullptr, CERT_EINVAL, "n_scenes must be >= 1");
+    for (int k = 0; k < 4; ++k)
+        if (cfg->reserved[k]) return fail(nullptr, CERT_EINVAL, "reserved fields must be zero");
+    if (!(cfg->cell_scale >= 0.0f) || !std::isfinite(cfg->cell_scale))
+        return fail(nullptr, CERT_EINVAL, "cell_scale must be finite and >= 0");
+    if (cfg->policy < 0 || cfg->policy > STRAT_REB)
+        return fail(nullptr, CERT_EINVAL, "policy must be AUTO, INCREMENTAL or REBUILD");
+    std::vector<int64_t> off;
+    if (cfg->offsets) {
+        off.assign(cfg->offsets, cfg->offsets + cfg->n_scenes + 1);
+    } else {
+        if (cfg->n_scenes != 1) return fail(nullptr, CERT_EINVAL, "offsets required when n_scenes > 1");
+        off = {0, cfg->n_total};
+    }
+    if (off[0] != 0) return fail(nullptr, CERT_EINVAL, "offsets[0] must be 0");
+    for (int s = 0; s < cfg->n_scenes; ++s)
+        if (off[s + 1] - off[s] < 3) return fail(nullptr, CERT_EINVAL, "every scene needs at least 3 points");
+    if (off.back() >= (int64_t(1) << 31) - kScanTile) return fail(nullptr, CERT_EINVAL, "too many points");
+
+    cert_ctx *c = new cert_ctx();
+    c->dim = cfg->dim;
+    c->S = cfg->n_scenes;
+    c->N = off.back();
+    c->cell_scale = cfg->cell_scale > 0.0f ? cfg->cell_scale : 1.5f;
+    c->policy = cfg->policy == STRAT_AUTO ? STRAT_INC : cfg->policy;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // ---- per-scene layout
+    c->h_sp.resize(c->S);
+    int64_t boff = 0, hoff = 0, apoff = 0, total_qb = 0;
+    for (int k = 0; k < c->S; ++k) total_qb += ceil_div(off[k + 1] - off[k], kApQBlock);
+    const int64_t nch_all = std::min<int64_t>(64, std::max<int64_t>(1, ceil_div(148 * 8, total_qb)));
+    std::vector<APItem> items;
+    for (int k = 0; k < c->S; ++k) {
+        SceneParams &p = c->h_sp[k];
+        std::memset(&p, 0, sizeof(p));
+        const int64_t n = off[k + 1] - off[k];
+        p.pt_off = (int32_t)off[k];
+        p.n = (int32_t)n;
+        const int T = next_pow2(std::max<int64_t>(n, 16));
+        p.bucket_off = (int32_t)boff;
+        p.bucket_mask = T - 1;
+        boff += T;
+        p.g_h = entropy_res(n, c->dim);
+        p.h_off = (int32_t)hoff;
+        hoff += (int64_t)std::pow((double)p.g_h, (double)c->dim) + 0.5;
+        p.g_default = std::max(1, (int)std::floor(std::pow(n / 2.0, 1.0 / c->dim)));
+        const int nch = (int)std::min<int64_t>(nch_all, ceil_div(n, 256));
+        p.ap_nch = nch;
+        p.ap_chunk = (int32_t)ceil_div(n, nch);
+        p.ap_off = (int32_t)apoff;
+        apoff += n * nch;
+        const int nqb = (int)ceil_div(n, kApQBlock);
+        for (int ch = 0; ch < nch; ++ch)
+            for (int qb = 0; qb < nqb; ++qb) items.push_back({k, qb, ch, 0});
+    }
+    c->n_buckets = (int)boff;
+    c->n_buckets_pad = (int)ceil_div(boff + 1, kScanTile) * kScanTile;
+    c->ntiles_b = c->n_buckets_pad / kScanTile;
+    c->ntiles_p = (int)ceil_div(c->N, kScanTile);
+    c->n_h = hoff;
+    c->ap_P = apoff;
+    c->n_ap_items = (int)items.size();
+
+    // ---- carve one allocation
+    const int64_t N = c->N, S = c->S, Npad = ceil_div(N, kScanTile) * kScanTile;
+    Carver cv;
+    const size_t o_sp = cv.take<SceneParams>(S), o_st = cv.take<SceneState>(S),
+                 o_res = cv.take<cert_scene_result>(S), o_status = cv.take<uint32_t>(4),
+                 o_fstart = cv.take<int32_t>(S + 1), o_scene = cv.take<int32_t>(N),
+                 o_pos0 = cv.take<float4>(N), o_pos1 = cv.take<float4>(N), o_nn = cv.take<int32_t>(N),
+                 o_nn2 = cv.take<int32_t>(N), o_d1 = cv.take<float>(N), o_d2 = cv.take<float>(N),
+                 o_L = cv.take<float>(N), o_hcell = cv.take<int32_t>(N), o_front = cv.take<int32_t>(N),
+                 o_inF = cv.take<uint8_t>(Npad), o_failed = cv.take<uint8_t>(Npad),
+                 o_sflag = cv.take<uint8_t>(Npad), o_brank = cv.take<int2>(N), o_sorted = cv.take<float4>(N),
+                 o_bstart = cv.take<int32_t>(c->n_buckets_pad), o_nlogn = cv.take<double>(kNlognTable),
+                 o_stage = cv.take<float>(N * c->dim), o_items = cv.take<APItem>(items.size()),
+                 o_pd = cv.take<float>(3 * apoff), o_pj = cv.take<int32_t>(3 * apoff),
+                 o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16);
+    cv.off = (cv.off + 255) & ~size_t(255);
+    const size_t zero_begin = cv.off;
+    const size_t o_acc = cv.take<SceneAcc>(S), o_ctr = cv.take<uint32_t>(4),
+                 o_tb = cv.take<uint64_t>(c->ntiles_b), o_tp = cv.take<uint64_t>(c->ntiles_p),
+                 o_bcount = cv.take<int32_t>(c->n_buckets_pad), o_hocc = cv.take<int32_t>(hoff),
+                 o_hfail = cv.take<int32_t>(hoff), o_hcand = cv.take<int32_t>(hoff);
+    c->zero_bytes = cv.off - zero_begin;
+    c->blob_bytes = cv.off;
+    cudaError_t e = cudaMalloc((void **)&c->blob, c->blob_bytes);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? CERT_ENOMEM : CERT_ECUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    char *b = c->blob;
+    c->sp = (SceneParams *)(b + o_sp);
+    c->st = (SceneState *)(b + o_st);
+    c->res = (cert_scene_result *)(b + o_res);
+    c->status = (uint32_t *)(b + o_status);
+    c->fstart = (int32_t *)(b + o_fstart);
+    c->scene_of = (int32_t *)(b + o_scene);
+    c->pos[0] = (float4 *)(b + o_pos0);
+    c->pos[1] = (float4 *)(b + o_pos1);
+    c->nn = (int32_t *)(b + o_nn);
+    c->nn2 = (int32_t *)(b + o_nn2);
+    c->d1sq = (float *)(b + o_d1);
+    c->d2sq = (float *)(b + o_d2);
+    c->L = (float *)(b + o_L);
+    c->hcell = (int32_t *)(b + o_hcell);
+    c->frontier = (int32_t *)(b + o_front);
+    c->inF = (uint8_t *)(b + o_inF);
+    c->failed = (uint8_t *)(b + o_failed);
+    c->sflag = (uint8_t *)(b + o_sflag);
+    c->brank = (int2 *)(b + o_brank);
+    c->sorted = (float4 *)(b + o_sorted);
+    c->bucket_start = (int32_t *)(b + o_bstart);
+    c->nlogn = (double *)(b + o_nlogn);
+    c->stage = (float *)(b + o_stage);
+    c->ap_items = (APItem *)(b + o_items);
+    c->ap_pd = (float *)(b + o_pd);
+    c->ap_pj = (int32_t *)(b + o_pj);
+    c->sel_params = (float *)(b + o_selp);
+    c->sel_norm = (float *)(b + o_seln);
+    c->zero = b + zero_begin;
+    c->acc = (SceneAcc *)(b + o_acc);
+    c->tile_ctr = (uint32_t *)(b + o_ctr);
+    c->tstat_b = (uint64_t *)(b + o_tb);
+    c->tstat_p = (uint64_t *)(b + o_tp);
+    c->bucket_count = (int32_t *)(b + o_bcount);
+    c->hocc = (int32_t *)(b + o_hocc);
+    c->hfail = (int32_t *)(b + o_hfail);
+    c->hcand = (int32_t *)(b + o_hcand);
+
+    // ---- host-built tables
+    std::vector<int32_t> scene_of(N);
+    for (int k = 0; k < c->S; ++k)
+        for (int64_t i = off[k]; i < off[k + 1]; ++i) scene_of[i] = k;
+    std::vector<double> nlogn(kNlognTable);
+    nlogn[0] = 0.0;
+    for (int k = 1; k < kNlognTable; ++k) nlogn[k] = (double)k * std::log((double)k);
+    std::vector<SceneState> st0(S);
+    for (int k = 0; k < c->S; ++k) {
+        std::memset(&st0[k], 0, sizeof(SceneState));
+        st0[k].g_cur = st0[k].g_next = c->h_sp[k].g_default;
+        st0[k].strategy = STRAT_INC;
+    }
+    cert_status rc = CERT_OK;
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (rc != CERT_OK || bytes == 0) return;
+        cudaError_t e2 = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+        if (e2 != cudaSuccess) rc = cuda_fail(c, "cudaMemcpyAsync", e2);
+    };
+    up(c->sp, c->h_sp.data(), S * sizeof(SceneParams));
+    up(c->st, st0.data(), S * sizeof(SceneState));
+    up(c->scene_of, scene_of.data(), N * sizeof(int32_t));
+    up(c->nlogn, nlogn.data(), kNlognTable * sizeof(double));
+    up(c->ap_items, items.data(), items.size() * sizeof(APItem));
+    if (rc == CERT_OK) {
+        // padding bytes of the flag arrays and the result block start at zero
+        cudaError_t e3 = cudaMemsetAsync(c->inF, 0, Npad, s);
+        if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->failed, 0, Npad, s);
+        if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->sflag, 0, Npad, s);
+        if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->res, 0, S * sizeof(cert_scene_result), s);
+        if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->status, 0, 4 * sizeof(uint32_t), s);
+        if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->fstart, 0, (S + 1) * sizeof(int32_t), s);
+        if (e3 != cudaSuccess) rc = cuda_fail(c, "cudaMemsetAsync", e3);
+    }
+    if (rc == CERT_OK) rc = run_full(c, MODE_INIT, d_pos, s);
+    if (rc != CERT_OK) {
+        g_err = c->err;
+        cudaStreamSynchronize(s);
+        cudaFree(c->blob);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return CERT_OK;
+}
+
+cert_status cert_step(cert_ctx *c, const float *d_pos_new, float eps, int32_t strategy, cert_views *out,
+                      void *stream)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    if (!d_pos_new) return fail(c, CERT_EINVAL, "positions are NULL");
+    if (!(eps >= 0.0f) || !std::isfinite(eps)) return fail(c, CERT_EINVAL, "eps must be finite and >= 0");
+    if (strategy < STRAT_AUTO || strategy > STRAT_ALL) return fail(c, CERT_EINVAL, "unknown strategy");
+    cudaStream_t s = (cudaStream_t)stream;
+    StepArgs a = make_args(c, MODE_STEP);
+    a.pos_in = d_pos_new;
+    a.pos_old = c->pos[c->cur];
+    a.pos_new = c->pos[c->cur ^ 1];
+    a.declared_eps = eps;
+    a.strategy = strategy;
+    a.ntiles_p = c->ntiles_p;
+    cudaEvent_t *ev = nullptr;
+    if (c->prof_on && c->prof_n < c->prof_max) ev = &c->prof_ev[size_t(c->prof_n++) * (CERT_N_PHASES + 1)];
+    auto mark = [&](int k) -> cudaError_t { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
+    CK(c, mark(0));
+    CK(c, cudaMemsetAsync(c->zero, 0, c->zero_bytes, s));
+    CK(c, mark(1));
+    CK(c, launch_step_phase(a, PH_PREPARE, s));
+    CK(c, mark(2));
+    CK(c, launch_step_phase(a, PH_SCAN, s));
+    CK(c, mark(3));
+    CK(c, launch_step_phase(a, PH_SELECT, s));
+    CK(c, mark(4));
+    if (strategy == STRAT_ALL) {
+        APArgs ap;
+        std::memset(&ap, 0, sizeof(ap));
+        ap.dim = c->dim;
+        ap.pos = a.pos_new;
+        ap.sp = c->sp;
+        ap.items = c->ap_items;
+        ap.n_items = c->n_ap_items;
+        ap.pd = c->ap_pd;
+        ap.pj = c->ap_pj;
+        ap.P = c->ap_P;
+        ap.status = c->status;
+        CK(c, launch_allpairs(ap, s));
+        CK(c, mark(5));
+        APMergeOut mo;
+        std::memset(&mo, 0, sizeof(mo));
+        mo.step_mode = 1;
+        mo.step = a;
+        CK(c, launch_allpairs_merge(ap, mo, c->N, s));
+    } else {
+        CK(c, launch_step_phase(a, PH_SCATTER, s));
+        CK(c, mark(5));
+        CK(c, launch_step_phase(a, PH_SEARCH, s));
+    }
+    CK(c, mark(6));
+    CK(c, launch_step_phase(a, PH_FINALIZE, s));
+    CK(c, mark(7));
+    c->cur ^= 1;
+    c->last = s;
+    c->stepped = true;
+    if (out) cert_get_views(c, out);
+    return CERT_OK;
+}
+
+cert_status cert_step_host(cert_ctx *c, const float *h_pos_new, float eps, int32_t strategy,
+                           cert_scene_result *h_scenes, void *stream)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    if (!h_pos_new) return fail(c, CERT_EINVAL, "positions are NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(c, cudaMemcpyAsync(c->stage, h_pos_new, size_t(c->N) * c->dim * sizeof(float), cudaMemcpyHostToDevice, s));
+    cert_status rc = cert_step(c, c->stage, eps, strategy, nullptr, stream);
+    if (rc != CERT_OK) return rc;
+    if (h_scenes)
+        CK(c, cudaMemcpyAsync(h_scenes, c->res, size_t(c->S) * sizeof(cert_scene_result),
+                              cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    return CERT_OK;
+}
+
+cert_status cert_rebuild(cert_ctx *c, void *stream)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    return run_full(c, MODE_REBUILD, nullptr, (cudaStream_t)stream);
+}
+
+cert_status cert_get_views(const cert_ctx *c, cert_views *out)
+{
+    if (!c || !out) return fail(const_cast<cert_ctx *>(c), CERT_EINVAL, "NULL argument");
+    out->nn = c->nn;
+    out->d1sq = c->d1sq;
+    out->d2sq = c->d2sq;
+    out->cell = c->hcell;
+    out->frontier = c->frontier;
+    out->failed = c->failed;
+    out->scenes = c->res;
+    out->n_total = c->N;
+    out->n_scenes = c->S;
+    out->dim = c->dim;
+    return CERT_OK;
+}
+
+cert_status cert_sync_result(cert_ctx *c, cert_scene_result *h_scenes)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    CK(c, cudaStreamSynchronize(c->last));
+    if (h_scenes) CK(c, cudaMemcpy(h_scenes, c->res, size_t(c->S) * sizeof(cert_scene_result), cudaMemcpyDeviceToHost));
+    uint32_t st = 0;
+    CK(c, cudaMemcpy(&st, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    CK(c, cudaMemset(c->status, 0, sizeof(uint32_t)));
+    if (st & ST_TIMEOUT) return fail(c, CERT_ETIMEOUT, "a bounded device wait gave up");
+    if (st & ST_NONFINITE) return fail(c, CERT_EINVAL, "non-finite coordinate in the positions");
+    if (st & ST_EBOUND) return fail(c, CERT_EBOUND, "measured eps_t exceeded the declared eps");
+    return CERT_OK;
+}
+
+cert_status cert_distances(cert_ctx *c, float *d_d1, float *d_d2, void *stream)
+{
+    if (!c || !d_d1 || !d_d2) return fail(c, CERT_EINVAL, "NULL argument");
+    CK(c, launch_distances(c->d1sq, c->d2sq, d_d1, d_d2, (int)c->N, (cudaStream_t)stream));
+    return CERT_OK;
+}
+
+cert_status cert_profile_begin(cert_ctx *c, int32_t max_steps)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    if (max_steps < 1 || max_steps > (1 << 20)) return fail(c, CERT_EINVAL, "max_steps out of range");
+    const size_t need = size_t(max_steps) * (CERT_N_PHASES + 1);
+    while (c->prof_ev.size() < need) {
+        cudaEvent_t e;
+        CK(c, cudaEventCreate(&e));
+        c->prof_ev.push_back(e);
+    }
+    c->prof_max = max_steps;
+    c->prof_n = 0;
+    c->prof_on = true;
+    return CERT_OK;
+}
+
+cert_status cert_profile_end(cert_ctx *c, float *h_ms, int32_t max_steps, int32_t *n_steps)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    c->prof_on = false;
+    const int n = std::min(c->prof_n, std::max(0, (int)max_steps));
+    if (n_steps) *n_steps = n;
+    if (n > 0) CK(c, cudaEventSynchronize(c->prof_ev[size_t(n - 1) * (CERT_N_PHASES + 1) + CERT_N_PHASES]));
+    for (int k = 0; k < n && h_ms; ++k) {
+        cudaEvent_t *ev = &c->prof_ev[size_t(k) * (CERT_N_PHASES + 1)];
+        for (int ph = 0; ph < CERT_N_PHASES; ++ph) {
+            float ms = 0.0f;
+            CK(c, cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]));
+            h_ms[size_t(k) * CERT_N_PHASES + ph] = ms;
+        }
+    }
+    c->prof_n = 0;
+    return CERT_OK;
+}
+
+void cert_destroy(cert_ctx *c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    cudaFree(c->blob);
+    delete c;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- cert_allpairs
+
+namespace certk {
+__global__ void k_write_params(SceneParams *dst, SceneParams v)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
+}
+}  // namespace certk
+
+extern "C" cert_status cert_allpairs(const float *d_pos, int64_t n, int32_t dim, const int32_t *d_queries,
+                                     int64_t nq, int32_t *d_nn, float *d_d1sq, float *d_d2sq, void *stream)
+{
+    if (!d_pos || !d_nn || !d_d1sq || !d_d2sq) return fail(nullptr, CERT_EINVAL, "NULL argument");
+    if (dim != 2 && dim != 3) return fail(nullptr, CERT_EINVAL, "dim must be 2 or 3");
+    if (n < 3 || n >= (int64_t(1) << 31) / 2) return fail(nullptr, CERT_EINVAL, "need 3 <= n < 2^30");
+    if (!d_queries) nq = n;
+    if (nq < 0 || nq >= (int64_t(1) << 31) / 2) return fail(nullptr, CERT_EINVAL, "bad query count");
+    if (nq == 0) return CERT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nqb = (int)ceil_div(nq, kApQBlock);
+    const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(148 * 8, nqb), ceil_div(n, 256)));
+    SceneParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.pt_off = 0;
+    p.n = (int32_t)n;
+    p.ap_off = 0;
+    p.ap_nch = nch;
+    p.ap_chunk = (int32_t)ceil_div(n, nch);
+    const long long P = (long long)nq * nch;
+    Carver cv;
+    const size_t o_pos = cv.take<float4>(n), o_sp = cv.take<SceneParams>(1), o_st = cv.take<uint32_t>(4),
+                 o_pd = cv.take<float>(3 * P), o_pj = cv.take<int32_t>(3 * P);
+    char *scratch = nullptr;
+    CK((cert_ctx *)nullptr, cudaMallocAsync((void **)&scratch, cv.off, s));
+    float4 *pos4 = (float4 *)(scratch + o_pos);
+    SceneParams *dsp = (SceneParams *)(scratch + o_sp);
+    uint32_t *status = (uint32_t *)(scratch + o_st);
+    cudaError_t e = cudaMemsetAsync(status, 0, 16, s);
+    if (e == cudaSuccess) {
+        k_write_params<<<1, 32, 0, s>>>(dsp, p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_pack(d_pos, (int)n, dim, pos4, status, s);
+    APArgs ap;
+    std::memset(&ap, 0, sizeof(ap));
+    ap.dim = dim;
+    ap.pos = pos4;
+    ap.sp = dsp;
+    ap.items = nullptr;
+    ap.nqb = nqb;
+    ap.n_items = nqb * nch;
+    ap.queries = d_queries;
+    ap.nq_list = (int)nq;
+    ap.pd = (float *)(scratch + o_pd);
+    ap.pj = (int32_t *)(scratch + o_pj);
+    ap.P = P;
+    ap.status = status;
+    if (e == cudaSuccess) e = launch_allpairs(ap, s);
+    APMergeOut mo;
+    std::memset(&mo, 0, sizeof(mo));
+    mo.nn = d_nn;
+    mo.d1sq = d_d1sq;
+    mo.d2sq = d_d2sq;
+    if (e == cudaSuccess) e = launch_allpairs_merge(ap, mo, nq, s);
+    cudaError_t e2 = cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, "cert_allpairs launch", e);
+    if (e2 != cudaSuccess) return cuda_fail(nullptr, "cudaFreeAsync", e2);
+    return CERT_OK;
+}

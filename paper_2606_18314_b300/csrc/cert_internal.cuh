@@ -1,0 +1,241 @@
+// cert_internal.cuh -- device-side building blocks of the certificate step.
+//
+// Shared by the CUDA translation units of libcert.so only.  Arithmetic on
+// squared distances is the fixed FP32 order of the public header (cert.h):
+// D(i,j) = ((dx*dx + dy*dy) + dz*dz), dx = x_j - x_i, every operation an
+// explicit round-to-nearest intrinsic so that no FMA contraction can occur.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace certk {
+
+constexpr int kThreads = 256;
+constexpr int kScanItems = 8;                          // items per thread in a scan tile
+constexpr int kScanTile = kThreads * kScanItems;       // 2048 items per tile
+constexpr int kSearchChunk = kThreads;                 // sorted slots per search CTA
+constexpr int kMedianSample = 1024;                    // points sampled for the medians
+constexpr int kMaxSearchRes = 2048;                    // search-grid cells per axis, cap
+constexpr int kWidenCap = 6;                           // ring radius beyond which a scene is scanned linearly
+constexpr uint32_t kSpinLimit = 1u << 22;              // bounded device waits
+constexpr int kNlognTable = 1 << 16;                   // k ln k table entries (FP64)
+
+// Latched device status bits (returned by cert_sync_result).
+enum : uint32_t { ST_TIMEOUT = 1u, ST_NONFINITE = 2u, ST_EBOUND = 4u };
+
+// Step kernel modes.
+enum : int { MODE_INIT = 0, MODE_STEP = 1, MODE_REBUILD = 2 };
+
+// Strategies (values of cert_strategy).
+enum : int { STRAT_AUTO = 0, STRAT_INC = 1, STRAT_REB = 2, STRAT_ALL = 3 };
+
+// Constant per-scene description (uploaded once at init).
+struct SceneParams {
+    int32_t pt_off, n;             // points [pt_off, pt_off + n)
+    int32_t bucket_off, bucket_mask;  // hashed search-grid buckets [bucket_off, +mask+1)
+    int32_t h_off, g_h;            // entropy grid: cells [h_off, h_off + g_h^dim), g_h per axis
+    int32_t ap_off, ap_nch;        // all-pairs partials: base index, chunks per query
+    int32_t ap_chunk, g_default;   // all-pairs chunk length; default search resolution
+    int32_t pad0, pad1;
+};
+
+// Per-scene state carried across steps.
+struct SceneState {
+    int32_t g_cur, g_next;         // search-grid cells per axis (this step, next step)
+    int32_t strategy;              // strategy applied this step
+    int32_t prev_nfront;           // previous step's |F|
+    float prev_fail_ratio;         // previous n_failed / max(1, n_frontier)
+    float prev_pred_ratio;         // previous selector output ln t_inc - ln t_reb
+    float med_c, med_d2;           // truncated medians of the pre-step certificates
+    float pred_inc, pred_reb;
+    int32_t pad0, pad1;
+};
+
+// Per-scene accumulators, zeroed at the start of every step.
+struct SceneAcc {
+    uint32_t eps_bits;             // max squared displacement (bit pattern, >= 0)
+    int32_t occ;                   // occupied entropy cells (C)
+    int32_t n_failed, n_missed;
+    int32_t failed_cells, frontier_cells;
+    int32_t n_searched, pad;
+    double s_fail;                 // sum over cells of n ln n, failures
+    double s_front;                // sum over cells of n ln n, detected frontier
+};
+
+struct Top3 {
+    float d0, d1, d2;
+    int j0, j1, j2;
+};
+
+// ----------------------------------------------------------------------------- arithmetic
+
+template <int DIM>
+__device__ __forceinline__ float sqdist(const float4 a, const float4 b)
+{
+    // a = point i (the query), b = point j; differences are (j - i).
+    const float dx = __fsub_rn(b.x, a.x);
+    const float dy = __fsub_rn(b.y, a.y);
+    float s = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+    if (DIM == 3) {
+        const float dz = __fsub_rn(b.z, a.z);
+        s = __fadd_rn(s, __fmul_rn(dz, dz));
+    }
+    return s;
+}
+
+// Cell coordinate of one axis: floor(x * g) clamped to [0, g-1].
+__device__ __forceinline__ int cell_coord(float x, int g, float gf)
+{
+    const float t = __fmul_rn(x, gf);
+    if (!(t >= 0.0f)) return 0;
+    if (t >= gf) return g - 1;
+    return (int)floorf(t);
+}
+
+template <int DIM>
+__device__ __forceinline__ uint32_t row_hash(int cy, int cz)
+{
+    uint32_t h = (uint32_t)cy * 0x9E3779B1u;
+    if (DIM == 3) h ^= (uint32_t)cz * 0x85EBCA77u;
+    return h;
+}
+
+__device__ __forceinline__ bool key_less(float da, int ja, float db, int jb)
+{
+    return da < db || (da == db && ja < jb);
+}
+
+__device__ __forceinline__ void top3_reset(Top3 &t)
+{
+    t.d0 = t.d1 = t.d2 = __int_as_float(0x7f800000);
+    t.j0 = t.j1 = t.j2 = 0x7fffffff;
+}
+
+// Insert (D, j) keeping the three lexicographically smallest distinct keys.
+// A candidate index already held is ignored (a hashed bucket may be visited twice).
+__device__ __forceinline__ void top3_insert(Top3 &t, float D, int j)
+{
+    if (!key_less(D, j, t.d2, t.j2)) return;
+    if (j == t.j0 || j == t.j1) return;
+    if (key_less(D, j, t.d1, t.j1)) {
+        t.d2 = t.d1;
+        t.j2 = t.j1;
+        if (key_less(D, j, t.d0, t.j0)) {
+            t.d1 = t.d0;
+            t.j1 = t.j0;
+            t.d0 = D;
+            t.j0 = j;
+        } else {
+            t.d1 = D;
+            t.j1 = j;
+        }
+    } else {
+        t.d2 = D;
+        t.j2 = j;
+    }
+}
+
+// Conservative lower bound on sqrt(x): correctly rounded down, then shrunk by
+// 2^-20 relative to absorb the rounding of the squared distance itself.
+__device__ __forceinline__ float sqrt_lower(float x)
+{
+    return __fmul_rd(__fsqrt_rd(x), 1.0f - 0x1p-20f);
+}
+
+__device__ __forceinline__ float eps_of(const SceneAcc *acc, int s)
+{
+    return __fsqrt_rn(__uint_as_float(acc[s].eps_bits));
+}
+
+// n ln n increment when a histogram count goes old -> old + 1 (FP64).
+__device__ __forceinline__ double nlogn_step(const double *tab, int old)
+{
+    if (old + 1 < kNlognTable) return tab[old + 1] - tab[old];
+    const double a = (double)old, b = (double)(old + 1);
+    return b * log(b) - a * log(a);
+}
+
+// ----------------------------------------------------------------------------- memory order
+
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ----------------------------------------------------------------------------- warp helpers
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Lanes of a warp holding consecutive points form contiguous runs of equal
+// scene id (scenes are contiguous ranges).  Each helper reduces within the run
+// and lets the run's lowest lane issue one atomic.  s < 0 marks an idle lane.
+__device__ __forceinline__ unsigned scene_run_mask(int s)
+{
+    return __match_any_sync(kFull, s);
+}
+
+__device__ __forceinline__ bool run_leader(unsigned mask)
+{
+    return (int)(threadIdx.x & 31) == __ffs(mask) - 1;
+}
+
+__device__ __forceinline__ int run_sum_i32(unsigned mask, int v)
+{
+    return (int)__reduce_add_sync(mask, (unsigned)v);
+}
+
+__device__ __forceinline__ unsigned run_max_u32(unsigned mask, unsigned v)
+{
+    return __reduce_max_sync(mask, v);
+}
+
+__device__ __forceinline__ double run_sum_f64(unsigned mask, double v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double w = __shfl_down_sync(kFull, v, o);
+        if (lane + o < 32 && ((mask >> (lane + o)) & 1u)) v += w;
+    }
+    return v;  // complete in the run's lowest lane
+}
+
+// ----------------------------------------------------------------------------- block scan
+
+// Exclusive scan of one value per thread across a 256-thread block; returns
+// the exclusive prefix, and the block total through *total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total, uint32_t *smem_warp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < kThreads / 32) ? smem_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kThreads / 32) smem_warp[lane] = w;  // inclusive warp prefixes
+    }
+    __syncthreads();
+    const uint32_t warp_base = warp ? smem_warp[warp - 1] : 0u;
+    *total = smem_warp[kThreads / 32 - 1];
+    return warp_base + x - v;
+}
+
+}  // namespace certk

@@ -1,0 +1,103 @@
+// cert_launch.h -- argument blocks and launch wrappers shared by the
+// translation units of libcert.so (host code calls these; kernels live in
+// step_kernels.cu, allpairs.cu and mlp.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cert.h"
+
+namespace certk {
+
+struct SceneParams;
+struct SceneState;
+struct SceneAcc;
+
+enum : int { PH_PREPARE = 0, PH_SCAN, PH_SELECT, PH_SCATTER, PH_SEARCH, PH_FINALIZE };
+
+// Everything a step kernel may touch.  Passed by value as a kernel parameter.
+struct StepArgs {
+    int mode;                      // MODE_INIT / MODE_STEP / MODE_REBUILD
+    int dim;
+    int n_total, n_scenes;
+    const float *pos_in;           // caller positions [n][dim] (INIT, STEP)
+    const float4 *pos_old;         // previous positions (STEP)
+    float4 *pos_new;               // positions of this step (written in INIT/STEP)
+    const int32_t *scene_of;       // [n] scene of every point
+    const SceneParams *sp;
+    SceneState *st;
+    SceneAcc *acc;
+    uint32_t *status;
+    // hashed search grid (counting sort by bucket)
+    int32_t *bucket_count;         // [n_buckets_pad]
+    int32_t *bucket_start;         // [n_buckets_pad]
+    int2 *brank;                   // [n] (bucket, rank in bucket)
+    float4 *sorted;                // [n] positions in bucket order, .w = point index bits
+    uint8_t *sflag;                // [n_pad] by sorted slot: 1 = search this point
+    // certificates
+    int32_t *nn, *nn2;
+    float *d1sq, *d2sq, *L;
+    // step outputs
+    int32_t *hcell, *hocc, *hfail, *hcand;
+    uint8_t *inF, *failed;
+    int32_t *frontier, *fstart;
+    // chained-scan state
+    uint64_t *tstat_b, *tstat_p;
+    uint32_t *tile_ctr;
+    int ntiles_b, ntiles_p;
+    const double *nlogn;
+    cert_scene_result *res;
+    float declared_eps;
+    int strategy, policy;
+    float cell_scale;
+    const float *sel_params;       // selector weights (NULL: none loaded)
+    const float *sel_norm;         // feature mean[8], 1/std[8]
+};
+
+cudaError_t launch_step_phase(const StepArgs &a, int phase, cudaStream_t st);
+cudaError_t launch_distances(const float *d1sq, const float *d2sq, float *d1, float *d2, int n,
+                             cudaStream_t st);
+
+// ---------------------------------------------------------------- all-pairs
+
+// Work item of the all-pairs kernel: scene, query block, j-chunk.
+struct APItem {
+    int32_t s, qb, chunk, pad;
+};
+
+struct APArgs {
+    int dim;
+    const float4 *pos;             // points in index order
+    const SceneParams *sp;         // per scene: pt_off, n, ap_off, ap_nch, ap_chunk
+    const APItem *items;           // one per block; NULL: scene 0, item = (b % nqb, b / nqb)
+    int n_items;
+    int nqb;                       // query blocks of scene 0 when items == NULL
+    const int32_t *queries;        // NULL: every point of each scene; else list (scene 0, local indices)
+    int nq_list;                   // length of the list
+    float *pd;                     // partial keys [3][P]
+    int32_t *pj;                   // partial indices [3][P]
+    long long P;
+    uint32_t *status;
+};
+
+// Outputs of the merge: ABI mode writes (nn, d1^2, d2^2) of each query; step
+// mode writes the full extended certificate of every point plus the audit.
+struct APMergeOut {
+    int32_t *nn;
+    float *d1sq, *d2sq;
+    int step_mode;                 // 1: StepArgs fields below are used
+    StepArgs step;
+};
+
+constexpr int kApThreads = 128;
+constexpr int kApQ = 4;                        // queries per thread
+constexpr int kApQBlock = kApThreads * kApQ;   // queries per block
+constexpr int kApTile = 2048;                  // candidates staged per shared-memory tile
+
+cudaError_t launch_allpairs(const APArgs &a, cudaStream_t st);
+cudaError_t launch_allpairs_merge(const APArgs &a, const APMergeOut &o, long long n_queries_total,
+                                  cudaStream_t st);
+cudaError_t launch_pack(const float *pos, int n, int dim, float4 *out, uint32_t *status, cudaStream_t st);
+
+}  // namespace certk

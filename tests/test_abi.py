@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point the
+headers declare, and rejects bad host arguments before touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2606_18314_b300 import build as cbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    cbuild.build()
+    from paper_2606_18314_b300 import cert
+    return cert.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(cert_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["cert_init", "cert_step", "cert_rebuild", "cert_allpairs", "cert_sync_result",
+                     "cert_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_symbol():
+    from paper_2606_18314_b300 import cert
+    assert set(declared_functions()) <= set(cert.EXPORTS)
+
+
+def test_version_string(L):
+    from paper_2606_18314_b300 import cert
+    assert "sm_103a" in cert.cert_version()
+
+
+def test_host_argument_validation_without_gpu(L):
+    from paper_2606_18314_b300 import cert
+    h = ctypes.c_void_p()
+    # NULL config / NULL positions / bad dim are rejected before any CUDA call
+    assert L.cert_init(ctypes.byref(h), None, None, None) == cert.CERT_EINVAL
+    cfg = cert.cert_config()
+    cfg.dim = 4
+    cfg.n_scenes = 1
+    cfg.n_total = 10
+    assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
+    assert b"dim" in L.cert_last_error(None)
+    cfg.dim = 3
+    cfg.n_total = 2
+    assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
+    cfg.n_total = 10
+    cfg.reserved[0] = 1
+    assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
+    cfg.reserved[0] = 0
+    cfg.policy = 3
+    assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
+    assert L.cert_step(None, None, ctypes.c_float(1e-3), 1, None, None) == cert.CERT_EINVAL
+    assert L.cert_allpairs(None, 10, 3, None, 0, None, None, None, None) == cert.CERT_EINVAL
+    assert L.cert_allpairs(ctypes.c_void_p(16), 2, 3, None, 0, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                           ctypes.c_void_p(16), None) == cert.CERT_EINVAL
+    assert L.cert_sync_result(None, None) == cert.CERT_EINVAL
+
+
+def test_struct_layouts_match_header():
+    from paper_2606_18314_b300 import cert
+    # cert_scene_result: 2 doubles + 16 four-byte fields
+    assert ctypes.sizeof(cert.cert_scene_result) == 16 + 16 * 4
+    assert ctypes.sizeof(cert.cert_config) == 4 + 4 + 8 + 8 + 4 + 4 + 16

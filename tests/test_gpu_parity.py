@@ -1,0 +1,312 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element
+by element on the same seeded inputs.  Bit-exact for nn, d1^2, d2^2, cells,
+frontier membership and order, failure marks and every count; H and H_cand
+within 1e-6 absolute of the oracle's FP64 value (the tolerance of the
+certificate-maintenance target)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_18314_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+H_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2606_18314_b300 import build
+    build.build()
+    return t
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def assert_cert_equal(views, ref, lo=0, hi=None, tag=""):
+    hi = ref.nn.shape[0] + lo if hi is None else hi
+    nn = host(views["nn"][lo:hi])
+    d1 = host(views["d1sq"][lo:hi])
+    d2 = host(views["d2sq"][lo:hi])
+    bad = np.nonzero((nn != ref.nn) | (d1.view(np.uint32) != ref.d1sq.view(np.uint32)) |
+                     (d2.view(np.uint32) != ref.d2sq.view(np.uint32)))[0]
+    assert bad.size == 0, (f"{tag}: {bad.size} certificates differ, first {bad[:5]} "
+                           f"gpu={nn[bad[:3]]},{d1[bad[:3]]},{d2[bad[:3]]} "
+                           f"ref={ref.nn[bad[:3]]},{ref.d1sq[bad[:3]]},{ref.d2sq[bad[:3]]}")
+
+
+def assert_step_equal(ctx, res, views, r, s=0, tag=""):
+    """Compare one scene's step outputs with an oracle StepResult."""
+    lo, hi = int(ctx.offsets[s]), int(ctx.offsets[s + 1])
+    sc = res[s]
+    assert_cert_equal(views, r.cert, lo, hi, tag)
+    assert np.float32(sc["eps_t"]) == r.eps_t, tag
+    nF = int(sc["n_frontier"])
+    F = host(views["frontier"][int(sc["frontier_start"]):int(sc["frontier_start"]) + nF])
+    assert nF == len(r.frontier) and np.array_equal(F, r.frontier), f"{tag}: frontier differs"
+    assert np.array_equal(host(views["failed"][lo:hi]).astype(bool), r.failed), f"{tag}: failed marks"
+    assert np.array_equal(host(views["cell"][lo:hi]), r.cell), f"{tag}: cells"
+    assert int(sc["n_failed"]) == r.n_failed, tag
+    assert int(sc["n_missed"]) == r.n_missed == 0, tag
+    assert int(sc["n_false"]) == r.n_false, tag
+    assert int(sc["failed_cells"]) == r.m, tag
+    assert int(sc["frontier_cells"]) == r.m_cand, tag
+    assert int(sc["occupied_cells"]) == r.C, tag
+    assert int(sc["grid_res"]) == r.g_h, tag
+    assert abs(float(sc["H"]) - r.H) <= H_TOL, (tag, float(sc["H"]), r.H)
+    assert abs(float(sc["H_cand"]) - r.H_cand) <= H_TOL, (tag, float(sc["H_cand"]), r.H_cand)
+    assert np.float32(sc["med_c"]) == r.med_c, (tag, sc["med_c"], r.med_c)
+
+
+# ----------------------------------------------------------------------------- all-pairs
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("n", [3, 4, 5, 37, 511, 512, 513, 2049, 5000])
+def test_allpairs_bit_exact(torch, n, dim):
+    from paper_2606_18314_b300 import cert
+    rng = np.random.default_rng(n * 10 + dim)
+    pts = rng.random((n, dim)).astype(np.float32)
+    ref = oracle.top2(pts)
+    nn, d1, d2 = cert.cert_allpairs(dev(torch, pts))
+    assert_cert_equal({"nn": nn, "d1sq": d1, "d2sq": d2}, ref, tag=f"allpairs n={n}")
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_allpairs_ties_and_duplicates(torch, dim):
+    from paper_2606_18314_b300 import cert
+    rng = np.random.default_rng(5)
+    # coarse dyadic grid: many exact ties and duplicate points
+    pts = (rng.integers(0, 5, size=(3000, dim)) / 4.0).astype(np.float32)
+    ref = oracle.top2(pts)
+    nn, d1, d2 = cert.cert_allpairs(dev(torch, pts))
+    assert_cert_equal({"nn": nn, "d1sq": d1, "d2sq": d2}, ref, tag="ties")
+
+
+def test_allpairs_query_list(torch):
+    from paper_2606_18314_b300 import cert
+    rng = np.random.default_rng(9)
+    pts = rng.random((20000, 3)).astype(np.float32)
+    q = rng.choice(20000, 1500, replace=False).astype(np.int32)
+    ref = oracle.top2_queries(pts, q)
+    nn, d1, d2 = cert.cert_allpairs(dev(torch, pts), dev(torch, q))
+    assert_cert_equal({"nn": nn, "d1sq": d1, "d2sq": d2}, ref, tag="queries")
+
+
+# ----------------------------------------------------------------------------- init / rebuild
+
+@pytest.mark.parametrize("family", scenes.ALL_FAMILIES)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_init_certificates_bit_exact(torch, family, dim):
+    from paper_2606_18314_b300 import cert
+    m = scenes.Motion(family, 3000, dim, 1e-3, seed=2)
+    p = m.frame()
+    ctx = cert.Context(dev(torch, p))
+    assert_cert_equal(ctx.views(), oracle.top2(p), tag=f"init {family}")
+    ctx.rebuild()
+    assert_cert_equal(ctx.views(), oracle.top2(p), tag=f"rebuild {family}")
+    ctx.sync()
+
+
+# ----------------------------------------------------------------------------- step loops
+
+def run_loop(torch, motion, steps, strategy, check_every=1):
+    from paper_2606_18314_b300 import cert
+    p = motion.frame()
+    ctx = cert.Context(dev(torch, p))
+    ref = oracle.top2(p)
+    for t in range(steps):
+        q = motion.advance()
+        ctx.step(dev(torch, q), motion.eps, strategy)
+        res, _ = ctx.sync()
+        r = oracle.step(p, q, ref)
+        if t % check_every == 0 or t == steps - 1:
+            assert_step_equal(ctx, res, ctx.views(), r, tag=f"{motion.family} step {t} {strategy}")
+        assert int(res[0]["strategy"]) == cert.STRATEGY[strategy]
+        p, ref = q, r.cert
+    return ctx
+
+
+@pytest.mark.parametrize("strategy", ["incremental", "rebuild", "allpairs"])
+def test_plain_method_d2_n1000(torch, strategy):
+    """N=1000, d=2, uniform, 20 steps of the eps=1e-3 ball walk."""
+    run_loop(torch, scenes.Motion("uniform_brownian", 1000, 2, 1e-3, seed=1, steps=20), 20, strategy)
+
+
+@pytest.mark.parametrize("family", scenes.FAMILIES)
+@pytest.mark.parametrize("eps", [1e-4, 1e-3, 5e-3])
+def test_families_d3_incremental(torch, family, eps):
+    run_loop(torch, scenes.Motion(family, 4000, 3, eps, seed=3, steps=12), 12, "incremental")
+
+
+@pytest.mark.parametrize("family", scenes.FAMILIES)
+def test_families_d3_rebuild_and_d2(torch, family):
+    run_loop(torch, scenes.Motion(family, 3000, 3, 2e-3, seed=4, steps=6), 6, "rebuild")
+    run_loop(torch, scenes.Motion(family, 3000, 2, 2e-3, seed=5, steps=6), 6, "incremental")
+
+
+def test_strategies_agree_bitwise(torch):
+    from paper_2606_18314_b300 import cert
+    m = scenes.BatchMotion.mixed(n_scenes=5, lo=800, hi=3000, eps=2e-3, seed=7)
+    frames = m.frames(6)
+    outs = {}
+    for strat in ["incremental", "rebuild", "allpairs"]:
+        ctx = cert.Context(dev(torch, frames[0]), offsets=m.offsets)
+        for t in range(1, 7):
+            ctx.step(dev(torch, frames[t]), 2e-3, strat)
+        res, _ = ctx.sync()
+        v = ctx.views()
+        outs[strat] = [host(v[k]).copy() for k in ("nn", "d1sq", "d2sq", "failed", "cell")] + [
+            host(v["frontier"])[:int(res["n_frontier"].sum())].copy()]
+        ctx.close()
+    for strat in ["rebuild", "allpairs"]:
+        for a, b in zip(outs["incremental"], outs[strat]):
+            assert np.array_equal(a, b), strat
+
+
+# ----------------------------------------------------------------------------- batches
+
+def test_batched_scenes_match_oracle_per_scene(torch):
+    from paper_2606_18314_b300 import cert
+    m = scenes.BatchMotion.mixed(n_scenes=12, lo=300, hi=2500, eps=1e-3, seed=11)
+    off = m.offsets
+    frames = m.frames(5)
+    ctx = cert.Context(dev(torch, frames[0]), offsets=off)
+    refs = [oracle.top2(frames[0][off[s]:off[s + 1]]) for s in range(12)]
+    for t in range(1, 6):
+        ctx.step(dev(torch, frames[t]), 1e-3, "incremental" if t % 2 else "rebuild")
+        res, _ = ctx.sync()
+        views = ctx.views()
+        for s in range(12):
+            a, b = frames[t - 1][off[s]:off[s + 1]], frames[t][off[s]:off[s + 1]]
+            r = oracle.step(a, b, refs[s])
+            assert_step_equal(ctx, res, views, r, s=s, tag=f"scene {s} step {t}")
+            refs[s] = r.cert
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+def test_three_point_scenes_and_duplicates(torch):
+    from paper_2606_18314_b300 import cert
+    pts = np.array([[0.5, 0.5, 0.5]] * 3 + [[0.1, 0.2, 0.3], [0.1, 0.2, 0.3], [0.9, 0.9, 0.9]] +
+                   [[0.25, 0.25, 0.25], [0.5, 0.25, 0.25], [0.75, 0.25, 0.25], [1.0, 0.25, 0.25]],
+                   np.float32)
+    off = np.array([0, 3, 6, 10])
+    ctx = cert.Context(dev(torch, pts), offsets=off)
+    v = ctx.views()
+    for s in range(3):
+        ref = oracle.top2(pts[off[s]:off[s + 1]])
+        assert_cert_equal(v, ref, off[s], off[s + 1], tag=f"tiny {s}")
+    q = pts.copy()
+    q[:, 0] = np.minimum(q[:, 0] + np.float32(1e-4), 1.0)
+    ctx.step(dev(torch, q), 1e-4, "incremental")
+    res, _ = ctx.sync()
+    for s in range(3):
+        r = oracle.step(pts[off[s]:off[s + 1]], q[off[s]:off[s + 1]], oracle.top2(pts[off[s]:off[s + 1]]))
+        assert_step_equal(ctx, res, ctx.views(), r, s=s, tag=f"tiny step {s}")
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_lattice_ties(torch, dim):
+    from paper_2606_18314_b300 import cert
+    k = 14 if dim == 3 else 60
+    ax = (np.arange(k) * 2.0 ** -6 + 0.25).astype(np.float32)
+    grid = np.stack(np.meshgrid(*([ax] * dim), indexing="ij"), -1).reshape(-1, dim).astype(np.float32)
+    ctx = cert.Context(dev(torch, grid))
+    ref = oracle.top2(grid)
+    assert_cert_equal(ctx.views(), ref, tag="lattice")
+    # a zero step: every point has c = 0 and is in the frontier
+    ctx.step(dev(torch, grid), 0.0, "incremental")
+    res, _ = ctx.sync()
+    r = oracle.step(grid, grid, ref)
+    assert_step_equal(ctx, res, ctx.views(), r, tag="lattice step")
+    assert int(res[0]["n_frontier"]) == grid.shape[0]
+
+
+def test_isolated_point_needs_wide_search(torch):
+    """A point far from a dense cluster: its block must widen far beyond the
+    3^d neighbourhood (the bounded-search-cap failure the paper reports)."""
+    from paper_2606_18314_b300 import cert
+    rng = np.random.default_rng(2)
+    pts = np.concatenate([0.5 + 0.004 * rng.standard_normal((6000, 3)),
+                          [[0.02, 0.97, 0.03]], [[0.99, 0.01, 0.98]]]).astype(np.float32)
+    pts = np.clip(pts, 0, 1).astype(np.float32)
+    ctx = cert.Context(dev(torch, pts))
+    assert_cert_equal(ctx.views(), oracle.top2(pts), tag="isolated")
+    q = pts.copy()
+    q[-1] = [0.985, 0.015, 0.975]
+    ctx.step(dev(torch, q), 0.03, "incremental")
+    res, _ = ctx.sync()
+    assert_step_equal(ctx, res, ctx.views(), oracle.step(pts, q, oracle.top2(pts)), tag="isolated step")
+
+
+def test_points_outside_unit_box_are_clamped_exactly(torch):
+    from paper_2606_18314_b300 import cert
+    rng = np.random.default_rng(4)
+    pts = (rng.random((2000, 3)) * 1.4 - 0.2).astype(np.float32)
+    ctx = cert.Context(dev(torch, pts))
+    assert_cert_equal(ctx.views(), oracle.top2(pts), tag="outside")
+
+
+def test_tightness_construction_on_gpu(torch):
+    """Theorem A.1 construction embedded in a larger scene of far points."""
+    from paper_2606_18314_b300 import cert
+    rng = np.random.default_rng(1)
+    for eta in [3.5, 3.9375, 4.0, 4.5]:
+        far = (0.9 + 0.1 * rng.random((50, 3))).astype(np.float32)
+        e = 2.0 ** -10
+        line = np.array([[0.5, 0.5, 0.5], [0.75, 0.5, 0.5], [0.5 - (0.25 + eta * e), 0.5, 0.5]], np.float32)
+        p0 = np.concatenate([line, far]).astype(np.float32)
+        p1 = p0.copy()
+        p1[0, 0] -= e
+        p1[1, 0] += e
+        p1[2, 0] += e
+        ctx = cert.Context(dev(torch, p0))
+        ctx.step(dev(torch, p1), e, "incremental")
+        res, _ = ctx.sync()
+        r = oracle.step(p0, p1, oracle.top2(p0))
+        assert_step_equal(ctx, res, ctx.views(), r, tag=f"eta={eta}")
+        assert (0 in r.frontier) == (eta <= 4.0)
+
+
+def test_status_reporting(torch):
+    from paper_2606_18314_b300 import cert
+    m = scenes.Motion("uniform_brownian", 500, 3, 1e-3, seed=1)
+    ctx = cert.Context(dev(torch, m.frame()))
+    ctx.step(dev(torch, m.advance()), 1e-5, "incremental")   # declared eps far too small
+    _, rc = ctx.sync(raise_on_status=False)
+    assert rc == cert.CERT_EBOUND
+    _, rc = ctx.sync(raise_on_status=False)
+    assert rc == cert.CERT_OK                                   # latched status was cleared
+    bad = m.advance()
+    bad[7, 1] = np.nan
+    ctx.step(dev(torch, bad), 1e-3, "incremental")
+    _, rc = ctx.sync(raise_on_status=False)
+    assert rc == cert.CERT_EINVAL
+    with pytest.raises(cert.CertError):
+        ctx.step(dev(torch, m.frame()), -1.0, "incremental")
+    with pytest.raises(cert.CertError):
+        ctx.step(dev(torch, m.frame()), float("nan"), "incremental")
+
+
+def test_distances_and_host_step(torch):
+    from paper_2606_18314_b300 import cert
+    m = scenes.Motion("clustered_drift", 2000, 3, 1e-3, seed=6)
+    p = m.frame()
+    ctx = cert.Context(dev(torch, p))
+    d1, d2 = ctx.distances()
+    ref = oracle.top2(p)
+    assert np.array_equal(host(d1), np.sqrt(ref.d1sq))
+    assert np.array_equal(host(d2), np.sqrt(ref.d2sq))
+    q = m.advance()
+    out = ctx.step_host(q, 1e-3, "incremental")
+    r = oracle.step(p, q, ref)
+    assert int(out[0]["n_failed"]) == r.n_failed and int(out[0]["n_frontier"]) == len(r.frontier)
+    assert abs(float(out[0]["H"]) - r.H) <= H_TOL

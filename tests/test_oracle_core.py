@@ -284,6 +284,9 @@ def test_trunc_median(oracle_mod):
     v = np.array([1.2, 5.0, 0.7], np.float32)                  # median 1.2 -> 1.125 (3 mantissa bits)
     assert oracle_mod.trunc_median(v) == np.float32(1.125)
     assert oracle_mod.trunc_median(np.zeros(7, np.float32)) == 0.0
+    # only the first 1024 values are sampled
+    v = np.concatenate([np.full(1024, 3.0, np.float32), np.full(5000, 0.5, np.float32)])
+    assert oracle_mod.trunc_median(v) == np.float32(3.0)
 
 
 # --------------------------------------------------------------------------- full step / audit
