@@ -1,0 +1,423 @@
+"""Benchmark of the certificate-maintenance loop on B300 (one JSON line).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batched|c1|c2|c3] [--strategy auto|incremental|rebuild|allpairs]
+
+Metric: certified point-updates/s = (points of every scene) x (steps) / time,
+every certificate exact after each step.  A step is one pass of the whole
+path -- eps_t, frontier compaction, index rebuild, strategy selection, repair
+or rebuild, failure marks, H(F_t), audit -- over all scenes of the workload.
+
+Default workload: 512 independent scenes, N log-uniform in [500, 16000],
+d = 3, the five motion families mixed (scene s takes family s mod 5),
+eps = 1e-3.  The motion is a ping-pong over F+1 pre-generated frames
+(forward to frame F, back to frame 0), every step within eps; the cycle
+(2F steps) is captured once as a CUDA graph and replayed.
+
+Inputs are synthetic (seeded Philox motion families; no dataset).  The
+working set (positions, certificates, index) exceeds the 126 MB L2, so no
+explicit L2 flush is done between steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_18314_b300 import scenes  # noqa: E402
+
+METRIC = "certified point-updates/s"
+UNIT = "point-updates/s"
+KERNELS_PER_STEP = 6
+
+# Per-phase algorithmic (compulsory DRAM) bytes, see DESIGN.md "Roofline".
+#   prepare: read p' (4 dim) + p (16), write packed p' (16), (bucket, rank) (8), cell (4),
+#            bucket-count and cell-count atomics (8 + 8)
+#   scan:    read d1^2, d2^2 (8), write frontier flag (1) per point; bucket count read +
+#            start write (8) per bucket; frontier index (4) per frontier point
+#   scatter_refresh: read (bucket, rank) 8 + bucket start 4 + p' 16, write sorted 16 + flag 1;
+#            refreshed points: read flag 1 + nn, nn2 8 + L 4 + two neighbour positions 32,
+#            write nn, nn2, d1^2, d2^2, L 20 + failed 1
+#   search:  read flag (1) per point; per searched point read query 16 + old nn 4 + flag 1 +
+#            cell 4, write certificate 20 + failed 1
+PHASES = ["clear", "prepare", "scan", "select", "scatter_refresh", "search", "finalize"]
+
+
+def phase_bytes(ph, N, dim, n_buckets, n_front, n_searched, zero_bytes):
+    refreshed = N - n_searched
+    if ph == "clear":
+        return zero_bytes
+    if ph == "prepare":
+        return N * (4 * dim + 16 + 16 + 8 + 4 + 16)
+    if ph == "scan":
+        return N * 9 + n_buckets * 8 + n_front * 4
+    if ph == "scatter_refresh":
+        return N * (8 + 4 + 16 + 16 + 1) + refreshed * (1 + 8 + 4 + 32 + 20 + 1)
+    if ph == "search":
+        return N * 1 + n_searched * (16 + 4 + 1 + 4 + 20 + 1)
+    return 0
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(name, rank, frames, n_scenes=512):
+    if name == "batched":
+        bm = scenes.BatchMotion.mixed(n_scenes=n_scenes, dim=3, eps=1e-3, seed=4 + 1000 * rank, steps=100)
+        return bm.frames(frames), bm.offsets, 1e-3, {
+            "workload": f"batched-{n_scenes}-scenes", "scenes": n_scenes, "n_range": [500, 16000], "dim": 3,
+            "eps": 1e-3,
+            "families": list(scenes.FAMILIES)}
+    if name == "c2":
+        m = scenes.Motion("uniform_brownian", 16000, 3, 1e-3, seed=1 + rank, steps=200)
+        return m.frames(frames), np.array([0, 16000], np.int64), 1e-3, {
+            "workload": "single-scene-16000-d3", "scenes": 1, "n": 16000, "dim": 3, "eps": 1e-3,
+            "families": ["uniform_brownian"]}
+    if name == "c1":
+        m = scenes.Motion("uniform_brownian", 1000, 2, 1e-3, seed=1 + rank, steps=20)
+        return m.frames(frames), np.array([0, 1000], np.int64), 1e-3, {
+            "workload": "single-scene-1000-d2", "scenes": 1, "n": 1000, "dim": 2, "eps": 1e-3,
+            "families": ["uniform_brownian"]}
+    if name == "c3":
+        m = scenes.Motion("uniform_clusters", 262144, 3, 1e-4, seed=1 + rank, steps=100)
+        return m.frames(frames), np.array([0, 262144], np.int64), 1e-4, {
+            "workload": "single-scene-262144-d3-clusters", "scenes": 1, "n": 262144, "dim": 3, "eps": 1e-4,
+            "families": ["uniform_clusters"]}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def cycle_index(k, F):
+    """Frame targeted by step k of the ping-pong cycle over frames 0..F."""
+    r = k % (2 * F)
+    return r + 1 if r < F else 2 * F - r - 1
+
+
+def cpu_baseline(frames, offsets, dim, budget_s, per_step_budget=None, steps_exact=None):
+    """The oracle as it stands on this host's cores over a bounded sample:
+    whole scenes in a seeded random order (as many as fit the per-step budget,
+    at least one), stepped through the same frames."""
+    import oracle
+    S = len(offsets) - 1
+    sizes = np.diff(offsets)
+    order = np.random.default_rng(16).permutation(S)
+    # pick scenes whose brute-force cost fits the per-step budget (~1 ns per pair per thread)
+    thr = max(1, oracle.max_threads())
+    target = per_step_budget if per_step_budget else budget_s / 4.0
+    chosen, cost = [], 0.0
+    for s in order:
+        c = float(sizes[s]) ** 2 * 2.5e-9 / thr
+        if chosen and cost + c > target:
+            break
+        chosen.append(int(s))
+        cost += c
+    certs = {s: oracle.top2(frames[0][offsets[s]:offsets[s + 1]]) for s in chosen}
+    pts, steps, t0 = 0, 0, time.perf_counter()
+    F = frames.shape[0] - 1
+    prev = 0
+    while True:
+        k = cycle_index(steps, F)
+        for s in chosen:
+            a, b = frames[prev][offsets[s]:offsets[s + 1]], frames[k][offsets[s]:offsets[s + 1]]
+            r = oracle.step(a, b, certs[s])
+            certs[s] = r.cert
+            pts += b.shape[0]
+        prev = k
+        steps += 1
+        if steps_exact is not None:
+            if steps >= steps_exact:
+                break
+        elif time.perf_counter() - t0 >= budget_s or steps >= 10000:
+            break
+    el = time.perf_counter() - t0
+    return {"value": pts / el, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"{len(chosen)} of {S} scenes (seeded random, {int(sizes[chosen].sum())} points), "
+                      f"{steps} steps in {el:.1f} s"}, steps, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    frames, offsets, eps, cfg = make_workload(args.workload, 0, max(4, args.frames), args.scenes)
+    dim = frames.shape[2]
+    per_step = max(0.02, 120.0 / max(1, args.steps + args.warmup))
+    cb, steps, el = cpu_baseline(frames, offsets, dim, budget_s=per_step * args.steps, per_step_budget=per_step,
+                                 steps_exact=max(1, args.steps))
+    cfg = dict(cfg)
+    cfg["l2"] = "host oracle (no GPU)"
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * el / max(1, steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=64)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "c1", "c2", "c3"])
+    ap.add_argument("--strategy", default="incremental", choices=["auto", "incremental", "rebuild", "allpairs"])
+    ap.add_argument("--frames", type=int, default=32)
+    ap.add_argument("--scenes", type=int, default=512, help="scenes in the batched workload")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--prof-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--compare", action="store_true", help="also time the other plain strategies")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2606_18314_b300 import build as cbuild
+    from paper_2606_18314_b300 import cert
+    cbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    F = max(2, args.frames)
+    frames, offsets, eps, cfg = make_workload(args.workload, rank, F, args.scenes)
+    N, dim = frames.shape[1], frames.shape[2]
+    S = len(offsets) - 1
+    dev_frames = torch.from_numpy(frames).cuda()
+    strat = cert.STRATEGY[args.strategy]
+    stream = torch.cuda.current_stream()
+
+    ctx = cert.Context(dev_frames[0], offsets=offsets)
+    C = 2 * F
+    clock = [0]   # steps taken along the ping-pong cycle; the state sits at frame cycle_index(clock-1)
+
+    def do_step(strategy=strat):
+        ctx.step(dev_frames[cycle_index(clock[0], F)], eps, strategy)
+        clock[0] += 1
+
+    def to_cycle_start(strategy=strat):
+        while clock[0] % C:
+            do_step(strategy)
+
+    # warm-up: W eager steps, then complete the cycle so the graph starts at frame 0
+    W = max(3, args.warmup)
+    W = int(math.ceil(W / C) * C)
+    for _ in range(W):
+        do_step()
+    torch.cuda.synchronize()
+    ctx.sync()
+
+    K = args.steps
+    graphs = []
+    if not args.no_graph:
+        full, rem = divmod(K, C)
+        if full:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                for k in range(C):
+                    ctx.step(dev_frames[cycle_index(k, F)], eps, strat)
+            graphs.append((g, full))
+        if rem:
+            g2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g2):
+                for k in range(rem):
+                    ctx.step(dev_frames[cycle_index(k, F)], eps, strat)
+            graphs.append((g2, 1))
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    if graphs:
+        for g, reps in graphs:
+            for _ in range(reps):
+                g.replay()
+    else:
+        for k in range(K):
+            do_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    res, rc = ctx.sync(raise_on_status=False)
+    assert int(res["n_missed"].sum()) == 0, "safety rule missed a failure"
+    ms_max = ms
+    n_all = N
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        nt = torch.tensor([float(N)], device="cuda")
+        dist.all_reduce(nt)
+        n_all = int(nt.item())
+    value = n_all * K / (ms_max / 1e3)
+
+    if graphs:
+        clock[0] += K          # the replays advanced the state by K steps
+    to_cycle_start()
+    torch.cuda.synchronize()
+
+    # ---- per-phase timing (CUDA events on the launching stream), same workload, eager
+    P = max(1, args.prof_steps)
+    ctx.profile_begin(P)
+    counts = []
+    for k in range(P):
+        do_step()
+        r, _ = ctx.sync(raise_on_status=False)
+        counts.append((int(r["n_frontier"].sum()), int(r["n_searched"].sum()), int(r["n_failed"].sum())))
+    prof = ctx.profile_end()
+    mean_ms = prof.mean(axis=0)
+    peaks, peak_kind = load_peaks()
+    n_buckets = int(sum(1 << int(math.ceil(math.log2(max(int(n), 16)))) for n in np.diff(offsets)))
+    zero_bytes = 0
+    per_phase = {}
+    for j, ph in enumerate(PHASES):
+        byts = [phase_bytes(ph, N, dim, n_buckets, c[0], c[1], zero_bytes) for c in counts]
+        gbs = [b / (t * 1e-3) / 1e9 for b, t in zip(byts, prof[:, j]) if t > 0]
+        per_phase[ph] = {"ms": float(mean_ms[j]), "share": float(mean_ms[j] / mean_ms.sum()),
+                         "bytes": float(np.mean(byts)), "gbs": float(np.mean(gbs)) if gbs else 0.0}
+    dom = max((p for p in PHASES if p != "clear"), key=lambda p: per_phase[p]["ms"])
+    achieved = per_phase[dom]["bytes"] / (per_phase[dom]["ms"] * 1e-3) / 1e9
+    cnt = np.array(counts, dtype=np.float64)
+    step_counts = {"frontier_frac": float(cnt[:, 0].mean() / N), "searched_frac": float(cnt[:, 1].mean() / N),
+                   "failed_frac": float(cnt[:, 2].mean() / N)}
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
+                "phases": per_phase}
+
+    # ---- end to end through the public API with host buffers (pinned), per step H2D + D2H
+    E = max(1, min(args.e2e_steps, K))
+    host_frames = torch.from_numpy(frames).pin_memory()
+    out = np.zeros(S, cert.SCENE_DTYPE)
+    row_bytes = N * dim * 4
+    base_ptr = host_frames.data_ptr()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(E):
+        ctx.step_host_ptr(base_ptr + cycle_index(clock[0], F) * row_bytes, eps, strat, out)
+        clock[0] += 1
+    el = time.perf_counter() - t0
+    e2e = {"value": N * E / el * (n_all / N), "unit": UNIT, "h2d_bytes_per_step": row_bytes,
+           "d2h_bytes_per_step": int(S * cert.SCENE_DTYPE.itemsize), "steps": E}
+
+    compare = {}
+    if args.compare:
+        for other in ["incremental", "rebuild"]:
+            if other == args.strategy:
+                continue
+            so = cert.STRATEGY[other]
+            to_cycle_start(so)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for k in range(C):
+                do_step(so)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            compare[other] = N * C / (e0.elapsed_time(e1) / 1e3)
+        compare[args.strategy + " (timed above)"] = value
+
+    cb = None
+    if rank == 0 and args.cpu_seconds > 0:
+        cb, _, _ = cpu_baseline(frames, offsets, dim, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        cfg = dict(cfg)
+        cfg.update({"strategy": args.strategy, "graph": not args.no_graph, "frames": F + 1,
+                    "motion": "ping-pong over pre-generated frames, every step <= eps",
+                    "l2": "no flush: working set > 126 MB L2 (inputs larger than L2)",
+                    "parallelism": f"scene-replicas x{world}"})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
+                "cpu_baseline": cb, "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
+                "step_counts": step_counts,
+                "status": cert.STATUS_NAMES[rc] if 0 <= rc < len(cert.STATUS_NAMES) else rc}
+        if compare:
+            line["compare"] = compare
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

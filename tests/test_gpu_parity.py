@@ -206,7 +206,7 @@ def test_three_point_scenes_and_duplicates(torch):
         assert_cert_equal(v, ref, off[s], off[s + 1], tag=f"tiny {s}")
     q = pts.copy()
     q[:, 0] = np.minimum(q[:, 0] + np.float32(1e-4), 1.0)
-    ctx.step(dev(torch, q), 1e-4, "incremental")
+    ctx.step(dev(torch, q), 2e-4, "incremental")   # declared bound above the rounded displacement
     res, _ = ctx.sync()
     for s in range(3):
         r = oracle.step(pts[off[s]:off[s + 1]], q[off[s]:off[s + 1]], oracle.top2(pts[off[s]:off[s + 1]]))
