@@ -171,6 +171,25 @@ cert_status cert_profile_begin(cert_ctx *ctx, int32_t max_steps);
  * (milliseconds, CERT_N_PHASES per step) for *n_steps <= max_steps steps. */
 cert_status cert_profile_end(cert_ctx *ctx, float *h_ms, int32_t max_steps, int32_t *n_steps);
 
+/* cert_allpairs without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot let a library allocate device memory --
+ * a real-time loop whose memory is fixed at start-up, a host whose device
+ * memory belongs to another allocator (a framework's caching allocator, a
+ * pre-reserved pool), or code that must not wait on the driver's allocator.
+ * Same arguments, same results (bit for bit) as cert_allpairs.
+ *   - Scratch is one file-scope device array of 32 MiB, held by every GPU that
+ *     loads the library until the process exits.  A call needs about
+ *     16 n + 24 nq k bytes (k = number of j-chunks, 1 to 37); every call with
+ *     n = nq <= 524,000 fits.  A call that would not fit returns CERT_EINVAL
+ *     with the required size in cert_last_error(NULL); nothing is enqueued.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array: calls whose work overlaps on the GPU (for
+ *     example on two streams at once) race and must be serialised. */
+cert_status cert_allpairs_noalloc(const float *d_pos, int64_t n, int32_t dim, const int32_t *d_queries,
+                                  int64_t nq, int32_t *d_nn, float *d_d1sq, float *d_d2sq, void *stream);
+
 /* Release every resource of the context (synchronises it first). */
 void cert_destroy(cert_ctx *ctx);
 

@@ -65,7 +65,8 @@ _lib = None
 # every symbol include/cert.h declares (checked by the CPU tests)
 EXPORTS = ["cert_init", "cert_step", "cert_step_host", "cert_rebuild", "cert_get_views",
            "cert_sync_result", "cert_distances", "cert_allpairs", "cert_destroy", "cert_last_error",
-           "cert_version", "cert_profile_begin", "cert_profile_end"]
+           "cert_version", "cert_profile_begin", "cert_profile_end",
+           "cert_allpairs_noalloc"]
 N_PHASES = 7
 PHASE_NAMES = ["clear", "prepare", "scan", "select", "scatter_refresh", "search", "finalize"]
 
@@ -179,6 +180,34 @@ def cert_allpairs(pos, queries=None, stream=None):
                                ctypes.c_void_p(d1.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
                                _stream_ptr(stream)))
     return nn, d1, d2
+
+
+def cert_allpairs_noalloc(pos, queries=None, nn=None, d1sq=None, d2sq=None, stream=None):
+    """cert_allpairs_noalloc: the all-pairs top-2 using the library's fixed
+    scratch array, so the call itself allocates nothing on the device.  For
+    callers that must not allocate at all during the call, pass preallocated
+    outputs (nn int32, d1sq/d2sq float32, length n or len(queries))."""
+    import torch
+    fn = lib().cert_allpairs_noalloc
+    vp = ctypes.c_void_p
+    fn.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, ctypes.c_int64, vp, vp, vp, vp]
+    fn.restype = ctypes.c_int
+    dim = pos.shape[1]
+    pp = _dev_ptr(pos, "torch.float32", dim)
+    n = pos.shape[0]
+    if queries is not None:
+        qp, nq = _dev_ptr(queries, "torch.int32"), queries.shape[0]
+    else:
+        qp, nq = None, n
+    if nn is None:
+        nn = torch.empty(nq, dtype=torch.int32, device=pos.device)
+    if d1sq is None:
+        d1sq = torch.empty(nq, dtype=torch.float32, device=pos.device)
+    if d2sq is None:
+        d2sq = torch.empty(nq, dtype=torch.float32, device=pos.device)
+    _check(fn(pp, n, dim, qp, nq, vp(nn.data_ptr()), vp(d1sq.data_ptr()), vp(d2sq.data_ptr()),
+              _stream_ptr(stream)))
+    return nn, d1sq, d2sq
 
 
 class Context:

@@ -76,6 +76,12 @@ static cert_status fail(cert_ctx *ctx, cert_status code, const std::string &msg)
     return code;
 }
 
+// Lets other translation units of the library set the calling thread's
+// error text returned by cert_last_error(NULL).
+namespace certk {
+void record_thread_error(const char *msg) { g_err = msg; }
+}  // namespace certk
+
 static cert_status cuda_fail(cert_ctx *ctx, const char *what, cudaError_t e)
 {
     return fail(ctx, CERT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));

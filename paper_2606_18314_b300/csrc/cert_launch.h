@@ -100,4 +100,7 @@ cudaError_t launch_allpairs_merge(const APArgs &a, const APMergeOut &o, long lon
                                   cudaStream_t st);
 cudaError_t launch_pack(const float *pos, int n, int dim, float4 *out, uint32_t *status, cudaStream_t st);
 
+// Sets the text cert_last_error(NULL) returns on the calling thread.
+void record_thread_error(const char *msg);
+
 }  // namespace certk
