@@ -54,7 +54,9 @@ typedef enum {
     CERT_AUTO = 0,        /* per scene: the loaded selector's choice, else the policy */
     CERT_INCREMENTAL = 1, /* refresh safe certificates, grid-repair frontier (Alg. 1) */
     CERT_REBUILD = 2,     /* grid search for every point (O(N) rebuild)               */
-    CERT_ALLPAIRS = 3     /* exact all-pairs pass for every point (O(N^2))            */
+    CERT_ALLPAIRS = 3,    /* exact all-pairs pass for every point (O(N^2))            */
+    CERT_THRESHOLD = 4    /* per scene: incremental iff |F|/N < 1/ln N, else rebuild
+                             (Prop. 1 with the boundary P ~ 1/log N of Sec. 4)       */
 } cert_strategy;
 
 /* Batch description.  One context holds n_scenes independent scenes whose
@@ -156,6 +158,69 @@ cert_status cert_distances(cert_ctx *ctx, float *d_d1, float *d_d2, void *stream
  * Uses library-managed scratch from the stream-ordered allocator. */
 cert_status cert_allpairs(const float *d_pos, int64_t n, int32_t dim, const int32_t *d_queries,
                           int64_t nq, int32_t *d_nn, float *d_d1sq, float *d_d2sq, void *stream);
+
+/* Search-grid cell side of every scene = scale x (truncated median d2 of the
+ * scene's previous certificates); takes effect from the next step.  Only the
+ * speed depends on it: certificates are exact for any scale > 0. */
+cert_status cert_set_cell_scale(cert_ctx *ctx, float scale);
+float cert_get_cell_scale(const cert_ctx *ctx);
+
+/* Autotuner (the grid cell side of Sec. 2's uniform grid, chosen by timing):
+ * for each of the n_scales candidate scales, restore the current state, run
+ * one step on frame 0 (it builds the grid at that scale) and time steps on
+ * frames 1 .. n_frames-1 with CUDA events; keep the fastest scale, restore
+ * the state and write the per-candidate milliseconds to h_ms (may be NULL)
+ * and the chosen scale to *h_best (may be NULL).  Frames are device
+ * [n_total][dim] float32 arrays at d_frames + f * frame_stride, each within
+ * eps of the previous one (the first within eps of the current state).
+ * Synchronises; the first call allocates the snapshot buffer. */
+cert_status cert_autotune(cert_ctx *ctx, const float *d_frames, int64_t frame_stride, int32_t n_frames,
+                          float eps, int32_t strategy, const float *h_scales, int32_t n_scales, float *h_ms,
+                          float *h_best, void *stream);
+
+/* Copy the mutable state (positions, extended certificates, per-scene state
+ * and the last step's outputs) aside / put it back, so that several
+ * strategies can be run and timed from identical state.  The first
+ * cert_snapshot allocates its buffer (about 46 bytes per point); restore
+ * without a snapshot returns CERT_ESTATE.  Stream-ordered. */
+cert_status cert_snapshot(cert_ctx *ctx, void *stream);
+cert_status cert_restore(cert_ctx *ctx, void *stream);
+
+/* Selector features of the last step, h_feat[n_scenes][8] (synchronises):
+ * |F|/N, H_cand, ln N, d, ln(1 + eps_t/med_c), touched-cell fraction m_F/C,
+ * previous n_failed/max(1,|F|), previous predicted ln t_inc - ln t_reb. */
+cert_status cert_get_features(cert_ctx *ctx, float *h_feat);
+
+/* Number of selector parameters: W1[64][8], b1[64], W2[64][64], b2[64],
+ * W3[2][64], b3[2] in this order (float32). */
+#define CERT_MLP_PARAMS 4866
+
+/* Load the repair-strategy selector (no counterpart in the paper; the
+ * crossover it learns is the one Prop. 1 describes): an MLP 8-64-64-2 with
+ * ReLU whose outputs predict ln step time of incremental repair and of
+ * rebuild.  h_params[CERT_MLP_PARAMS]; h_norm[16] = feature mean[8] then
+ * 1/std[8] applied before the first layer.  With a selector loaded,
+ * CERT_AUTO picks, per scene and step, the strategy with the smaller
+ * prediction (non-finite predictions fall back to the policy).  h_params ==
+ * NULL unloads it.  Synchronises.  Never changes results, only the schedule. */
+cert_status cert_selector_load(cert_ctx *ctx, const float *h_params, const float *h_norm);
+
+/* Selector training and batch inference on the device (no counterpart in
+ * the paper).  X[n][8] raw features, normalised inside the kernels with
+ * d_norm[16] (mean[8], 1/std[8]); T[n][2] targets (ln t_inc, ln t_reb);
+ * Y[n][2] predictions.  cert_mlp_grad writes the gradient of
+ * mean((y - t)^2) over all rows and both outputs into d_grad[CERT_MLP_PARAMS]
+ * and the loss into *d_loss (may be NULL); it needs a caller workspace of
+ * cert_mlp_workspace_bytes(n) bytes; the gradient is summed in a fixed order
+ * (deterministic).  cert_mlp_adam applies one Adam update (Kingma & Ba) with
+ * bias correction for step t >= 1.  All three only enqueue work. */
+size_t cert_mlp_workspace_bytes(int64_t n);
+cert_status cert_mlp_forward(const float *d_params, const float *d_norm, const float *d_X, int64_t n,
+                             float *d_Y, void *stream);
+cert_status cert_mlp_grad(const float *d_params, const float *d_norm, const float *d_X, const float *d_T,
+                          int64_t n, float *d_grad, float *d_loss, void *d_work, size_t work_bytes, void *stream);
+cert_status cert_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int32_t t, float lr,
+                          float beta1, float beta2, float eps, void *stream);
 
 /* Number of timed phases per step (see cert_profile_end). */
 #define CERT_N_PHASES 7

@@ -20,9 +20,9 @@ LIB_PATH = os.path.join(HERE, "libcert.so")
 CERT_OK, CERT_EINVAL, CERT_ENOMEM, CERT_ECUDA, CERT_ETIMEOUT, CERT_EBOUND, CERT_ESTATE = range(7)
 STATUS_NAMES = ["CERT_OK", "CERT_EINVAL", "CERT_ENOMEM", "CERT_ECUDA", "CERT_ETIMEOUT", "CERT_EBOUND",
                 "CERT_ESTATE"]
-CERT_AUTO, CERT_INCREMENTAL, CERT_REBUILD, CERT_ALLPAIRS = range(4)
+CERT_AUTO, CERT_INCREMENTAL, CERT_REBUILD, CERT_ALLPAIRS, CERT_THRESHOLD = range(5)
 STRATEGY = {"auto": CERT_AUTO, "incremental": CERT_INCREMENTAL, "rebuild": CERT_REBUILD,
-            "allpairs": CERT_ALLPAIRS}
+            "allpairs": CERT_ALLPAIRS, "threshold": CERT_THRESHOLD}
 
 
 class cert_config(ctypes.Structure):
@@ -66,7 +66,10 @@ _lib = None
 EXPORTS = ["cert_init", "cert_step", "cert_step_host", "cert_rebuild", "cert_get_views",
            "cert_sync_result", "cert_distances", "cert_allpairs", "cert_destroy", "cert_last_error",
            "cert_version", "cert_profile_begin", "cert_profile_end",
-           "cert_allpairs_noalloc"]
+           "cert_allpairs_noalloc", "cert_set_cell_scale", "cert_get_cell_scale", "cert_autotune",
+           "cert_snapshot", "cert_restore", "cert_get_features", "cert_selector_load",
+           "cert_mlp_workspace_bytes", "cert_mlp_forward", "cert_mlp_grad", "cert_mlp_adam"]
+MLP_PARAMS = 4866
 N_PHASES = 7
 PHASE_NAMES = ["clear", "prepare", "scan", "select", "scatter_refresh", "search", "finalize"]
 
@@ -94,6 +97,22 @@ def lib():
     L.cert_last_error.restype = ctypes.c_char_p
     L.cert_version.argtypes = []
     L.cert_version.restype = ctypes.c_char_p
+    L.cert_set_cell_scale.argtypes = [vp, f32]
+    L.cert_get_cell_scale.argtypes = [vp]
+    L.cert_get_cell_scale.restype = f32
+    L.cert_autotune.argtypes = [vp, vp, i64, i32, f32, i32, vp, i32, vp, vp, vp]
+    L.cert_snapshot.argtypes = [vp, vp]
+    L.cert_restore.argtypes = [vp, vp]
+    L.cert_get_features.argtypes = [vp, vp]
+    L.cert_selector_load.argtypes = [vp, vp, vp]
+    L.cert_mlp_workspace_bytes.argtypes = [i64]
+    L.cert_mlp_workspace_bytes.restype = ctypes.c_size_t
+    L.cert_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.cert_mlp_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, ctypes.c_size_t, vp]
+    L.cert_mlp_adam.argtypes = [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp]
+    for name in ["cert_set_cell_scale", "cert_autotune", "cert_snapshot", "cert_restore", "cert_get_features",
+                 "cert_selector_load", "cert_mlp_forward", "cert_mlp_grad", "cert_mlp_adam"]:
+        getattr(L, name).restype = ctypes.c_int
     L.cert_profile_begin.argtypes = [vp, i32]
     L.cert_profile_end.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
     for name in ["cert_init", "cert_step", "cert_step_host", "cert_rebuild", "cert_get_views",
@@ -210,6 +229,30 @@ def cert_allpairs_noalloc(pos, queries=None, nn=None, d1sq=None, d2sq=None, stre
     return nn, d1sq, d2sq
 
 
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def cert_mlp_workspace_bytes(n):
+    return int(lib().cert_mlp_workspace_bytes(int(n)))
+
+
+def cert_mlp_forward(params, norm, X, Y, stream=None):
+    """Y[n][2] = selector(X[n][8]) on the device (all CUDA tensors, float32)."""
+    _check(lib().cert_mlp_forward(_ptr(params), _ptr(norm), _ptr(X), X.shape[0], _ptr(Y), _stream_ptr(stream)))
+
+
+def cert_mlp_grad(params, norm, X, T, grad, loss, work, stream=None):
+    """grad = d mean((selector(X) - T)^2) / d params; loss -> loss[0]."""
+    _check(lib().cert_mlp_grad(_ptr(params), _ptr(norm), _ptr(X), _ptr(T), X.shape[0], _ptr(grad), _ptr(loss),
+                               _ptr(work), work.numel() * work.element_size(), _stream_ptr(stream)))
+
+
+def cert_mlp_adam(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().cert_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(t), float(lr), float(beta1),
+                               float(beta2), float(eps), _stream_ptr(stream)))
+
+
 class Context:
     """A batch of scenes whose certificates are maintained on the GPU.
 
@@ -323,3 +366,47 @@ class Context:
         n = ctypes.c_int32(0)
         _check(lib().cert_profile_end(self.h, ctypes.c_void_p(out.ctypes.data), mx, ctypes.byref(n)), self.h)
         return out[:n.value]
+
+    # ---- tuning, snapshots, selector -------------------------------------------------
+    def set_cell_scale(self, scale):
+        _check(lib().cert_set_cell_scale(self.h, float(scale)), self.h)
+
+    def cell_scale(self):
+        return float(lib().cert_get_cell_scale(self.h))
+
+    def snapshot(self, stream=None):
+        _check(lib().cert_snapshot(self.h, _stream_ptr(stream)), self.h)
+
+    def restore(self, stream=None):
+        _check(lib().cert_restore(self.h, _stream_ptr(stream)), self.h)
+
+    def autotune(self, frames, eps, strategy=CERT_INCREMENTAL, scales=(1.0, 1.25, 1.5, 2.0, 2.5), stream=None):
+        """cert_autotune over consecutive device frames [F][n][dim]; returns (best, ms per scale)."""
+        if isinstance(strategy, str):
+            strategy = STRATEGY[strategy]
+        sc = np.ascontiguousarray(scales, np.float32)
+        ms = np.zeros(len(sc), np.float32)
+        best = ctypes.c_float(0.0)
+        stride = int(frames.shape[1] * frames.shape[2])
+        _check(lib().cert_autotune(self.h, _dev_ptr(frames.reshape(-1, self.dim), "torch.float32", self.dim),
+                                   stride, int(frames.shape[0]), float(eps), int(strategy),
+                                   ctypes.c_void_p(sc.ctypes.data), len(sc), ctypes.c_void_p(ms.ctypes.data),
+                                   ctypes.byref(best), _stream_ptr(stream)), self.h)
+        return float(best.value), ms
+
+    def features(self):
+        """Selector features of the last step, [n_scenes][8] (synchronises)."""
+        out = np.zeros((self.n_scenes, 8), np.float32)
+        _check(lib().cert_get_features(self.h, ctypes.c_void_p(out.ctypes.data)), self.h)
+        return out
+
+    def load_selector(self, params, norm):
+        """cert_selector_load: params[4866], norm[16] (host float32), or None to unload."""
+        if params is None:
+            _check(lib().cert_selector_load(self.h, None, None), self.h)
+            return
+        p = np.ascontiguousarray(params, np.float32)
+        nm = np.ascontiguousarray(norm, np.float32)
+        assert p.shape == (MLP_PARAMS,) and nm.shape == (16,)
+        _check(lib().cert_selector_load(self.h, ctypes.c_void_p(p.ctypes.data), ctypes.c_void_p(nm.ctypes.data)),
+               self.h)

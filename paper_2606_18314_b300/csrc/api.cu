@@ -50,6 +50,12 @@ struct cert_ctx {
     int32_t *ap_pj = nullptr;
     float *sel_params = nullptr, *sel_norm = nullptr;
     bool have_sel = false;
+    float *feat = nullptr;          // [S][8] selector features of the last step
+    // snapshot of the mutable state (allocated by the first cert_snapshot)
+    char *snap = nullptr;
+    size_t snap_bytes = 0;
+    int snap_cur = 0;
+    bool snap_valid = false;
     // zeroed at the start of every call that runs the pipeline
     char *zero = nullptr;
     size_t zero_bytes = 0;
@@ -167,7 +173,8 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.policy = c->policy;
     a.cell_scale = c->cell_scale;
     a.sel_params = c->have_sel ? c->sel_params : nullptr;
-    a.sel_norm = c->sel_norm;
+    a.sel_norm = c->have_sel ? c->sel_norm : nullptr;
+    a.feat = c->feat;
     return a;
 }
 
@@ -280,7 +287,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_bstart = cv.take<int32_t>(c->n_buckets_pad), o_nlogn = cv.take<double>(kNlognTable),
                  o_stage = cv.take<float>(N * c->dim), o_items = cv.take<APItem>(items.size()),
                  o_pd = cv.take<float>(3 * apoff), o_pj = cv.take<int32_t>(3 * apoff),
-                 o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16);
+                 o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16), o_feat = cv.take<float>(S * 8);
     cv.off = (cv.off + 255) & ~size_t(255);
     const size_t zero_begin = cv.off;
     const size_t o_acc = cv.take<SceneAcc>(S), o_ctr = cv.take<uint32_t>(4),
@@ -324,6 +331,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->ap_pj = (int32_t *)(b + o_pj);
     c->sel_params = (float *)(b + o_selp);
     c->sel_norm = (float *)(b + o_seln);
+    c->feat = (float *)(b + o_feat);
     c->zero = b + zero_begin;
     c->acc = (SceneAcc *)(b + o_acc);
     c->tile_ctr = (uint32_t *)(b + o_ctr);
@@ -345,6 +353,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     for (int k = 0; k < c->S; ++k) {
         std::memset(&st0[k], 0, sizeof(SceneState));
         st0[k].g_cur = st0[k].g_next = c->h_sp[k].g_default;
+        st0[k].inv_g = 1.0f / (float)st0[k].g_cur;
         st0[k].strategy = STRAT_INC;
     }
     cert_status rc = CERT_OK;
@@ -366,6 +375,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->res, 0, S * sizeof(cert_scene_result), s);
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->status, 0, 4 * sizeof(uint32_t), s);
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->fstart, 0, (S + 1) * sizeof(int32_t), s);
+        if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->feat, 0, S * 8 * sizeof(float), s);
         if (e3 != cudaSuccess) rc = cuda_fail(c, "cudaMemsetAsync", e3);
     }
     if (rc == CERT_OK) rc = run_full(c, MODE_INIT, d_pos, s);
@@ -386,7 +396,7 @@ cert_status cert_step(cert_ctx *c, const float *d_pos_new, float eps, int32_t st
     if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
     if (!d_pos_new) return fail(c, CERT_EINVAL, "positions are NULL");
     if (!(eps >= 0.0f) || !std::isfinite(eps)) return fail(c, CERT_EINVAL, "eps must be finite and >= 0");
-    if (strategy < STRAT_AUTO || strategy > STRAT_ALL) return fail(c, CERT_EINVAL, "unknown strategy");
+    if (strategy < STRAT_AUTO || strategy > STRAT_THR) return fail(c, CERT_EINVAL, "unknown strategy");
     cudaStream_t s = (cudaStream_t)stream;
     StepArgs a = make_args(c, MODE_STEP);
     a.pos_in = d_pos_new;
@@ -535,10 +545,144 @@ cert_status cert_profile_end(cert_ctx *c, float *h_ms, int32_t max_steps, int32_
     return CERT_OK;
 }
 
+cert_status cert_set_cell_scale(cert_ctx *c, float scale)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    if (!(scale > 0.0f) || !std::isfinite(scale)) return fail(c, CERT_EINVAL, "cell_scale must be finite and > 0");
+    c->cell_scale = scale;
+    return CERT_OK;
+}
+
+float cert_get_cell_scale(const cert_ctx *c) { return c ? c->cell_scale : 0.0f; }
+
+cert_status cert_get_features(cert_ctx *c, float *h_feat)
+{
+    if (!c || !h_feat) return fail(c, CERT_EINVAL, "NULL argument");
+    CK(c, cudaStreamSynchronize(c->last));
+    CK(c, cudaMemcpy(h_feat, c->feat, size_t(c->S) * 8 * sizeof(float), cudaMemcpyDeviceToHost));
+    return CERT_OK;
+}
+
+cert_status cert_selector_load(cert_ctx *c, const float *h_params, const float *h_norm)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    CK(c, cudaStreamSynchronize(c->last));
+    if (!h_params) {
+        c->have_sel = false;
+        return CERT_OK;
+    }
+    if (!h_norm) return fail(c, CERT_EINVAL, "feature normalisation is NULL");
+    for (int k = 0; k < CERT_MLP_PARAMS; ++k)
+        if (!std::isfinite(h_params[k])) return fail(c, CERT_EINVAL, "non-finite selector weight");
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(h_norm[k])) return fail(c, CERT_EINVAL, "non-finite feature normalisation");
+    CK(c, cudaMemcpy(c->sel_params, h_params, CERT_MLP_PARAMS * sizeof(float), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->sel_norm, h_norm, 16 * sizeof(float), cudaMemcpyHostToDevice));
+    c->have_sel = true;
+    return CERT_OK;
+}
+
+// Pieces of the mutable state a snapshot covers (device pointer, bytes).
+static std::vector<std::pair<void *, size_t>> snapshot_pieces(cert_ctx *c)
+{
+    const size_t N = size_t(c->N), S = size_t(c->S);
+    return {{c->pos[c->cur], N * sizeof(float4)},  {c->nn, N * 4},         {c->nn2, N * 4},
+            {c->d1sq, N * 4},                      {c->d2sq, N * 4},       {c->L, N * 4},
+            {c->st, S * sizeof(SceneState)},      {c->res, S * sizeof(cert_scene_result)},
+            {c->hcell, N * 4},                     {c->frontier, N * 4},   {c->fstart, (S + 1) * 4},
+            {c->failed, N},                        {c->inF, N},            {c->feat, S * 8 * 4}};
+}
+
+cert_status cert_snapshot(cert_ctx *c, void *stream)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    auto pieces = snapshot_pieces(c);
+    size_t need = 0;
+    for (auto &p : pieces) need += (p.second + 255) & ~size_t(255);
+    if (!c->snap) {
+        cudaError_t e = cudaMalloc((void **)&c->snap, need);
+        if (e != cudaSuccess) return fail(c, CERT_ENOMEM, std::string("snapshot buffer: ") + cudaGetErrorString(e));
+        c->snap_bytes = need;
+    }
+    size_t off = 0;
+    for (auto &p : pieces) {
+        CK(c, cudaMemcpyAsync(c->snap + off, p.first, p.second, cudaMemcpyDeviceToDevice, s));
+        off += (p.second + 255) & ~size_t(255);
+    }
+    c->snap_cur = c->cur;
+    c->snap_valid = true;
+    c->last = s;
+    return CERT_OK;
+}
+
+cert_status cert_restore(cert_ctx *c, void *stream)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    if (!c->snap_valid) return fail(c, CERT_ESTATE, "no snapshot taken");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->cur = c->snap_cur;
+    auto pieces = snapshot_pieces(c);
+    size_t off = 0;
+    for (auto &p : pieces) {
+        CK(c, cudaMemcpyAsync(p.first, c->snap + off, p.second, cudaMemcpyDeviceToDevice, s));
+        off += (p.second + 255) & ~size_t(255);
+    }
+    c->last = s;
+    return CERT_OK;
+}
+
+cert_status cert_autotune(cert_ctx *c, const float *d_frames, int64_t frame_stride, int32_t n_frames, float eps,
+                          int32_t strategy, const float *h_scales, int32_t n_scales, float *h_ms, float *h_best,
+                          void *stream)
+{
+    if (!c || !d_frames || !h_scales) return fail(c, CERT_EINVAL, "NULL argument");
+    if (n_frames < 2 || n_scales < 1 || frame_stride < c->N * c->dim)
+        return fail(c, CERT_EINVAL, "need n_frames >= 2, n_scales >= 1 and frame_stride >= n_total*dim");
+    for (int k = 0; k < n_scales; ++k)
+        if (!(h_scales[k] > 0.0f) || !std::isfinite(h_scales[k])) return fail(c, CERT_EINVAL, "bad candidate scale");
+    cudaStream_t s = (cudaStream_t)stream;
+    const float keep = c->cell_scale;
+    cert_status rc = cert_snapshot(c, stream);
+    if (rc != CERT_OK) return rc;
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    float best_ms = 0.0f, best = keep;
+    for (int k = 0; k < n_scales && rc == CERT_OK; ++k) {
+        rc = cert_restore(c, stream);
+        c->cell_scale = h_scales[k];
+        // the first step derives the search grid from the candidate scale
+        if (rc == CERT_OK) rc = cert_step(c, d_frames, eps, strategy, nullptr, stream);
+        if (rc == CERT_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = fail(c, CERT_ECUDA, "event");
+        for (int f = 1; f < n_frames && rc == CERT_OK; ++f)
+            rc = cert_step(c, d_frames + f * frame_stride, eps, strategy, nullptr, stream);
+        if (rc == CERT_OK && cudaEventRecord(e1, s) != cudaSuccess) rc = fail(c, CERT_ECUDA, "event");
+        float ms = 0.0f;
+        if (rc == CERT_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = fail(c, CERT_ECUDA, "event timing");
+        if (h_ms) h_ms[k] = ms;
+        if (rc == CERT_OK && (k == 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = h_scales[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cert_status rc2 = cert_restore(c, stream);
+    c->cell_scale = (rc == CERT_OK) ? best : keep;
+    if (h_best) *h_best = c->cell_scale;
+    if (rc == CERT_OK) rc = rc2;
+    // drop any status the probe steps latched (e.g. EBOUND from the caller's frames)
+    if (rc == CERT_OK) CK(c, cudaMemsetAsync(c->status, 0, sizeof(uint32_t), s));
+    return rc;
+}
+
 void cert_destroy(cert_ctx *c)
 {
     if (!c) return;
     cudaDeviceSynchronize();
+    if (c->snap) cudaFree(c->snap);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     cudaFree(c->blob);
     delete c;

@@ -17,7 +17,7 @@ constexpr int kScanTile = kThreads * kScanItems;       // 2048 items per tile
 constexpr int kSearchChunk = kThreads;                 // sorted slots per search CTA
 constexpr int kMedianSample = 1024;                    // points sampled for the medians
 constexpr int kMaxSearchRes = 2048;                    // search-grid cells per axis, cap
-constexpr int kWidenCap = 6;                           // ring radius beyond which a scene is scanned linearly
+constexpr int kMaxExtend = 16;                         // face extensions before a warp scans the scene
 constexpr uint32_t kSpinLimit = 1u << 22;              // bounded device waits
 constexpr int kNlognTable = 1 << 16;                   // k ln k table entries (FP64)
 
@@ -28,7 +28,7 @@ enum : uint32_t { ST_TIMEOUT = 1u, ST_NONFINITE = 2u, ST_EBOUND = 4u };
 enum : int { MODE_INIT = 0, MODE_STEP = 1, MODE_REBUILD = 2 };
 
 // Strategies (values of cert_strategy).
-enum : int { STRAT_AUTO = 0, STRAT_INC = 1, STRAT_REB = 2, STRAT_ALL = 3 };
+enum : int { STRAT_AUTO = 0, STRAT_INC = 1, STRAT_REB = 2, STRAT_ALL = 3, STRAT_THR = 4 };
 
 // Constant per-scene description (uploaded once at init).
 struct SceneParams {
@@ -49,7 +49,8 @@ struct SceneState {
     float prev_pred_ratio;         // previous selector output ln t_inc - ln t_reb
     float med_c, med_d2;           // truncated medians of the pre-step certificates
     float pred_inc, pred_reb;
-    int32_t pad0, pad1;
+    float inv_g;                   // 1/g_cur, rounded to nearest (face positions of the search)
+    int32_t pad0;
 };
 
 // Per-scene accumulators, zeroed at the start of every step.
@@ -93,12 +94,34 @@ __device__ __forceinline__ int cell_coord(float x, int g, float gf)
     return (int)floorf(t);
 }
 
-template <int DIM>
-__device__ __forceinline__ uint32_t row_hash(int cy, int cz)
+// Bucket of the first cell of row (cy, cz) of the search grid; the cells of a
+// row occupy consecutive buckets (mod T).  When the whole grid fits in the
+// bucket table (g^dim <= T) the mapping is the plain linear cell index and
+// buckets never mix cells; otherwise the row is placed by a 32-bit integer
+// finalizer (the MurmurHash3 fmix32 mixing steps) and collisions only add
+// candidates, never remove one.
+__device__ __forceinline__ uint32_t mix32(uint32_t x)
 {
-    uint32_t h = (uint32_t)cy * 0x9E3779B1u;
-    if (DIM == 3) h ^= (uint32_t)cz * 0x85EBCA77u;
-    return h;
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool grid_is_dense(int g, int T)
+{
+    const long long cells = (DIM == 3) ? (long long)g * g * g : (long long)g * g;
+    return cells <= (long long)T;
+}
+
+template <int DIM>
+__device__ __forceinline__ uint32_t row_base(int cy, int cz, int g, bool dense)
+{
+    if (dense) return (DIM == 3) ? (uint32_t)((cz * g + cy) * g) : (uint32_t)(cy * g);
+    return mix32((DIM == 3) ? ((uint32_t)cz * 0x10001u + (uint32_t)cy) : (uint32_t)cy);
 }
 
 __device__ __forceinline__ bool key_less(float da, int ja, float db, int jb)

@@ -52,7 +52,8 @@ struct StepArgs {
     int strategy, policy;
     float cell_scale;
     const float *sel_params;       // selector weights (NULL: none loaded)
-    const float *sel_norm;         // feature mean[8], 1/std[8]
+    const float *sel_norm;         // feature mean[8], 1/std[8] (NULL: none loaded)
+    float *feat;                   // [n_scenes][8] selector features of the last step
 };
 
 cudaError_t launch_step_phase(const StepArgs &a, int phase, cudaStream_t st);

@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(kThreads) k_prepare(const StepArgs a)
         const int cx = cell_coord(p.x, g, gf);
         const int cy = cell_coord(p.y, g, gf);
         const int cz = (DIM == 3) ? cell_coord(p.z, g, gf) : 0;
-        const int b = sp.bucket_off + (int)((row_hash<DIM>(cy, cz) + (uint32_t)cx) & (uint32_t)sp.bucket_mask);
+        const bool dense = grid_is_dense<DIM>(g, sp.bucket_mask + 1);
+        const int b = sp.bucket_off + (int)((row_base<DIM>(cy, cz, g, dense) + (uint32_t)cx) & (uint32_t)sp.bucket_mask);
         const int rank = atomicAdd(&a.bucket_count[b], 1);
         a.brank[i] = make_int2(b, rank);
         // entropy grid on the post-step position (Def. 2)
@@ -289,28 +290,34 @@ __global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
     if (a.mode == MODE_STEP) {
         strat = a.strategy;
         if (strat == STRAT_AUTO) strat = a.policy;
-        if (a.strategy == STRAT_AUTO && a.sel_params != nullptr) {
-            // ---- learned selector: 8 features -> MLP 8-64-64-2 -> argmin
-            if (threadIdx.x == 0) {
-                const SceneAcc acc = a.acc[s];
-                const SceneState st = a.st[s];
-                const int nF = a.fstart[s + 1] - a.fstart[s];
-                const float eps = eps_of(a.acc, s);
-                const double lnF = nF > 1 ? log((double)nF) : 0.0;
-                const double Hc = (nF > 1 && acc.occ > 1)
-                                      ? fmin(1.0, fmax(0.0, (lnF - acc.s_front / nF) / log((double)acc.occ)))
-                                      : 0.0;
-                float x[8];
-                x[0] = (float)nF / (float)sp.n;
-                x[1] = (float)Hc;
-                x[2] = logf((float)sp.n);
-                x[3] = (float)DIM;
-                x[4] = log1pf(fminf(eps / fmaxf(med_c, 1e-30f), 1e6f));
-                x[5] = acc.occ > 0 ? (float)acc.frontier_cells / (float)acc.occ : 0.0f;
-                x[6] = st.prev_fail_ratio;
-                x[7] = st.prev_pred_ratio;
-                for (int k = 0; k < 8; ++k) s_feat[k] = (x[k] - a.sel_norm[k]) * a.sel_norm[8 + k];
+        // ---- the eight selector features of this step (stored every step)
+        if (threadIdx.x == 0) {
+            const SceneAcc acc = a.acc[s];
+            const SceneState st = a.st[s];
+            const int nF = a.fstart[s + 1] - a.fstart[s];
+            const float eps = eps_of(a.acc, s);
+            const double lnF = nF > 1 ? log((double)nF) : 0.0;
+            const double Hc = (nF > 1 && acc.occ > 1)
+                                  ? fmin(1.0, fmax(0.0, (lnF - acc.s_front / nF) / log((double)acc.occ)))
+                                  : 0.0;
+            float x[8];
+            x[0] = (float)nF / (float)sp.n;                               // |F|/N
+            x[1] = (float)Hc;                                             // H of the detected frontier
+            x[2] = logf((float)sp.n);                                     // ln N
+            x[3] = (float)DIM;                                            // d
+            x[4] = log1pf(fminf(eps / fmaxf(med_c, 1e-30f), 1e6f));       // ln(1 + eps_t / med c)
+            x[5] = acc.occ > 0 ? (float)acc.frontier_cells / (float)acc.occ : 0.0f;  // touched-cell fraction
+            x[6] = st.prev_fail_ratio;                                    // previous failed / frontier
+            x[7] = st.prev_pred_ratio;                                    // previous predicted ln ratio
+            for (int k = 0; k < 8; ++k) {
+                a.feat[s * 8 + k] = x[k];
+                s_feat[k] = a.sel_norm ? (x[k] - a.sel_norm[k]) * a.sel_norm[8 + k] : x[k];
             }
+            // Prop. 1 rule with the boundary P ~ 1/ln N measured in Sec. 4
+            if (a.strategy == STRAT_THR) strat = (x[0] < 1.0f / x[2]) ? STRAT_INC : STRAT_REB;
+        }
+        if (a.strategy == STRAT_AUTO && a.sel_params != nullptr) {
+            // ---- learned selector: MLP 8-64-64-2 on the normalised features -> argmin
             __syncthreads();
             const float *W1 = a.sel_params, *b1 = W1 + 64 * 8, *W2 = b1 + 64, *b2 = W2 + 64 * 64,
                         *W3 = b2 + 64, *b3 = W3 + 2 * 64;
@@ -442,14 +449,27 @@ struct SearchCtx {
     int pt_off, n, boff, T;
     uint32_t mask;
     int g;
+    float inv_g;
+    bool dense;
 };
 
+// Visit the sorted slots [lo, hi), two candidate loads in flight.
 template <int DIM>
 __device__ __forceinline__ void visit_range(const SearchCtx &c, int lo, int hi, Top3 &t)
 {
     lo = max(lo, c.pt_off);          // a bucket range never leaves its scene
     hi = min(hi, c.pt_off + c.n);
-    for (int k = lo; k < hi; ++k) {
+    int k = lo;
+    for (; k + 1 < hi; k += 2) {
+        const float4 q0 = c.sorted[k];
+        const float4 q1 = c.sorted[k + 1];
+        const int j0 = __float_as_int(q0.w), j1 = __float_as_int(q1.w);
+        const float D0 = sqdist<DIM>(c.p, q0);
+        const float D1 = sqdist<DIM>(c.p, q1);
+        if (D0 <= t.d2 && j0 != c.gi) top3_insert(t, D0, j0);
+        if (D1 <= t.d2 && j1 != c.gi) top3_insert(t, D1, j1);
+    }
+    if (k < hi) {
         const float4 q = c.sorted[k];
         const int j = __float_as_int(q.w);
         const float D = sqdist<DIM>(c.p, q);
@@ -457,106 +477,200 @@ __device__ __forceinline__ void visit_range(const SearchCtx &c, int lo, int hi, 
     }
 }
 
+// Slot range(s) of the cells [xl, xh] of row (yr, zr).  A row's cells are
+// consecutive buckets; the second range is non-empty only when they wrap.
 template <int DIM>
-__device__ __forceinline__ void visit_row(const SearchCtx &c, int yr, int zr, int xl, int xh, Top3 &t)
+__device__ __forceinline__ void row_ranges(const SearchCtx &c, int yr, int zr, int xl, int xh, int &lo, int &hi,
+                                           int &lo2, int &hi2)
 {
+    lo = hi = lo2 = hi2 = 0;
     xl = max(xl, 0);
     xh = min(xh, c.g - 1);
-    if (xl > xh) return;
+    if (xl > xh || yr < 0 || yr >= c.g || zr < 0 || zr >= c.g) return;
     const int len = xh - xl + 1;
     if (len >= c.T) {
-        visit_range<DIM>(c, c.pt_off, c.pt_off + c.n, t);
+        lo = c.pt_off;
+        hi = c.pt_off + c.n;
         return;
     }
-    const int b0 = (int)((row_hash<DIM>(yr, zr) + (uint32_t)xl) & c.mask);
+    const int b0 = (int)((row_base<DIM>(yr, zr, c.g, c.dense) + (uint32_t)xl) & c.mask);
     if (b0 + len <= c.T) {
-        visit_range<DIM>(c, c.bstart[c.boff + b0], c.bstart[c.boff + b0 + len], t);
+        lo = c.bstart[c.boff + b0];
+        hi = c.bstart[c.boff + b0 + len];
     } else {
-        visit_range<DIM>(c, c.bstart[c.boff + b0], c.bstart[c.boff + c.T], t);
-        visit_range<DIM>(c, c.bstart[c.boff], c.bstart[c.boff + b0 + len - c.T], t);
+        lo = c.bstart[c.boff + b0];
+        hi = c.bstart[c.boff + c.T];
+        lo2 = c.bstart[c.boff];
+        hi2 = c.bstart[c.boff + b0 + len - c.T];
     }
 }
 
-// Lower bound on the distance from p to any point outside the block of cells
-// [c - r, c + r]^dim; +inf when every face of the block lies on the grid edge
-// (boundary cells are clamped and so extend to infinity).
 template <int DIM>
-__device__ __forceinline__ float face_distance(const float4 p, int cx, int cy, int cz, int r, int g, float inv_g)
+__device__ __forceinline__ void visit_row(const SearchCtx &c, int yr, int zr, int xl, int xh, Top3 &t)
 {
-    float f = __int_as_float(0x7f800000);
-    const int c3[3] = {cx, cy, cz};
-    const float p3[3] = {p.x, p.y, p.z};
-#pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-        if (c3[ax] - r > 0) f = fminf(f, __fsub_rn(p3[ax], __fmul_rn((float)(c3[ax] - r), inv_g)));
-        if (c3[ax] + r < g - 1) f = fminf(f, __fsub_rn(__fmul_rn((float)(c3[ax] + r + 1), inv_g), p3[ax]));
-    }
-    return f;
+    int lo, hi, lo2, hi2;
+    row_ranges<DIM>(c, yr, zr, xl, xh, lo, hi, lo2, hi2);
+    visit_range<DIM>(c, lo, hi, t);
+    if (hi2 > lo2) visit_range<DIM>(c, lo2, hi2, t);
 }
 
 constexpr float kFaceSlack = 0x1p-17f;   // >> FP error of cell assignment and face position
 
+// Thread-level grid search over a box of cells [x0,x1] x [y0,y1] x [z0,z1]
+// holding the query's cell.  It starts as the 3^d block of Algorithm 1 and
+// grows one cell layer at a time on the face nearest to the query -- the face
+// that limits the enclosure -- until the runner-up is provably enclosed (its
+// distance is below the distance to every face that is not on the grid
+// edge; boundary cells are clamped and extend to infinity), as in Cor. A.2.
+// Returns false after kMaxExtend layers; such a query is finished by a whole
+// warp (far pass of k_search).
 template <int DIM>
-__device__ __forceinline__ void grid_search(const SearchCtx &c, Top3 &t, float &Lout)
+__device__ __forceinline__ bool grid_search(const SearchCtx &c, Top3 &t, float &Lout, int2 *rng)
 {
     const float gf = (float)c.g;
-    const float inv_g = __frcp_rn(gf);
     const int cx = cell_coord(c.p.x, c.g, gf);
     const int cy = cell_coord(c.p.y, c.g, gf);
     const int cz = (DIM == 3) ? cell_coord(c.p.z, c.g, gf) : 0;
     top3_reset(t);
-    // ring 1: the 3^d block of Algorithm 1
-    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
-        const int zr = cz + dz;
-        if (zr < 0 || zr >= c.g) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int yr = cy + dy;
-            if (yr < 0 || yr >= c.g) continue;
-            visit_row<DIM>(c, yr, zr, cx - 1, cx + 1, t);
+    // The 3^d block.  Fetch every row's slot range first (independent loads),
+    // keep them in this thread's column of the shared range table, then walk
+    // all rows as one stream so that a warp runs max(sum of lengths) rather
+    // than sum(max of lengths) iterations.
+    constexpr int NR = (DIM == 3) ? 9 : 3;
+    int total = 0;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int yr = cy + (k % 3) - 1;
+        const int zr = (DIM == 3) ? cz + (k / 3) - 1 : 0;
+        int lo, hi, lo2, hi2;
+        row_ranges<DIM>(c, yr, zr, cx - 1, cx + 1, lo, hi, lo2, hi2);
+        if (hi2 > lo2) visit_range<DIM>(c, lo2, hi2, t);   // wrapped row: rare
+        lo = max(lo, c.pt_off);
+        hi = max(lo, min(hi, c.pt_off + c.n));
+        rng[k * kThreads] = make_int2(lo, hi);
+        total += hi - lo;
+    }
+    {
+        int k = 0;
+        int2 cur = rng[0];
+        for (int m = 0; m < total; ++m) {
+            while (cur.x >= cur.y) cur = rng[(++k) * kThreads];
+            const float4 q = c.sorted[cur.x++];
+            const int j = __float_as_int(q.w);
+            const float D = sqdist<DIM>(c.p, q);
+            if (D <= t.d2 && j != c.gi) top3_insert(t, D, j);
         }
     }
-    int r = 1;
-    for (;;) {
-        const float f0 = face_distance<DIM>(c.p, cx, cy, cz, r, c.g, inv_g);
-        if (isinf(f0)) {  // the block covers the whole grid: everything was visited
-            Lout = sqrt_lower(t.d2);
-            return;
-        }
-        const float f = __fsub_rd(f0, kFaceSlack);
-        if (t.j1 != 0x7fffffff && f > 0.0f &&
-            __fmul_ru(t.d1, 1.0f + 0x1p-19f) < __fmul_rd(f, f)) {  // runner-up provably enclosed
-            Lout = fminf(sqrt_lower(t.d2), f);
-            return;
-        }
-        ++r;
-        if (r > kWidenCap) {  // far from everything: scan the scene linearly
-            visit_range<DIM>(c, c.pt_off, c.pt_off + c.n, t);
-            Lout = sqrt_lower(t.d2);
-            return;
-        }
-        // shell at Chebyshev radius r
-        for (int dz = (DIM == 3 ? -r : 0); dz <= (DIM == 3 ? r : 0); ++dz) {
-            const int zr = cz + dz;
-            if (zr < 0 || zr >= c.g) continue;
-            for (int dy = -r; dy <= r; ++dy) {
-                const int yr = cy + dy;
-                if (yr < 0 || yr >= c.g) continue;
-                if (max(abs(dy), abs(dz)) == r) {
-                    visit_row<DIM>(c, yr, zr, cx - r, cx + r, t);
-                } else {
-                    visit_row<DIM>(c, yr, zr, cx - r, cx - r, t);
-                    visit_row<DIM>(c, yr, zr, cx + r, cx + r, t);
-                }
+
+    const int gm = c.g - 1;
+    int x0 = max(cx - 1, 0), x1 = min(cx + 1, gm);
+    int y0 = max(cy - 1, 0), y1 = min(cy + 1, gm);
+    int z0 = (DIM == 3) ? max(cz - 1, 0) : 0, z1 = (DIM == 3) ? min(cz + 1, gm) : 0;
+    const float inf = __int_as_float(0x7f800000);
+    for (int ext = 0;; ++ext) {
+        // distances to the six faces (+inf on the grid edge)
+        float f[6];
+        f[0] = x0 > 0 ? __fsub_rn(c.p.x, __fmul_rn((float)x0, c.inv_g)) : inf;
+        f[1] = x1 < gm ? __fsub_rn(__fmul_rn((float)(x1 + 1), c.inv_g), c.p.x) : inf;
+        f[2] = y0 > 0 ? __fsub_rn(c.p.y, __fmul_rn((float)y0, c.inv_g)) : inf;
+        f[3] = y1 < gm ? __fsub_rn(__fmul_rn((float)(y1 + 1), c.inv_g), c.p.y) : inf;
+        f[4] = (DIM == 3 && z0 > 0) ? __fsub_rn(c.p.z, __fmul_rn((float)z0, c.inv_g)) : inf;
+        f[5] = (DIM == 3 && z1 < gm) ? __fsub_rn(__fmul_rn((float)(z1 + 1), c.inv_g), c.p.z) : inf;
+        int side = 0;
+        float f0 = f[0];
+#pragma unroll
+        for (int k = 1; k < 6; ++k)
+            if (f[k] < f0) {
+                f0 = f[k];
+                side = k;
             }
+        if (isinf(f0)) {  // the box covers the whole grid: everything was visited
+            Lout = sqrt_lower(t.d2);
+            return true;
+        }
+        const float fs = __fsub_rd(f0, kFaceSlack);
+        if (t.j1 != 0x7fffffff && fs > 0.0f &&
+            __fmul_ru(t.d1, 1.0f + 0x1p-19f) < __fmul_rd(fs, fs)) {  // runner-up provably enclosed
+            Lout = fminf(sqrt_lower(t.d2), fs);
+            return true;
+        }
+        if (ext >= kMaxExtend) return false;
+        // grow the limiting face by one cell layer and visit the new cells
+        switch (side) {
+        case 0:
+        case 1: {
+            const int x = (side == 0) ? --x0 : ++x1;
+            for (int z = z0; z <= z1; ++z)
+                for (int y = y0; y <= y1; ++y) visit_row<DIM>(c, y, z, x, x, t);
+            break;
+        }
+        case 2:
+        case 3: {
+            const int y = (side == 2) ? --y0 : ++y1;
+            for (int z = z0; z <= z1; ++z) visit_row<DIM>(c, y, z, x0, x1, t);
+            break;
+        }
+        default: {
+            const int z = (side == 4) ? --z0 : ++z1;
+            for (int y = y0; y <= y1; ++y) visit_row<DIM>(c, y, z, x0, x1, t);
+            break;
+        }
         }
     }
+}
+
+// Merge the warp's per-lane top-3 lists (butterfly; every lane ends with the result).
+__device__ __forceinline__ void warp_merge_top3(Top3 &t)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float e0 = __shfl_xor_sync(kFull, t.d0, o), e1 = __shfl_xor_sync(kFull, t.d1, o),
+                    e2 = __shfl_xor_sync(kFull, t.d2, o);
+        const int k0 = __shfl_xor_sync(kFull, t.j0, o), k1 = __shfl_xor_sync(kFull, t.j1, o),
+                  k2 = __shfl_xor_sync(kFull, t.j2, o);
+        if (k0 != 0x7fffffff) top3_insert(t, e0, k0);
+        if (k1 != 0x7fffffff) top3_insert(t, e1, k1);
+        if (k2 != 0x7fffffff) top3_insert(t, e2, k2);
+    }
+}
+
+// Certificate write and failure audit of one searched point (thread level).
+struct SearchOut {
+    int changed, missed, first;
+    double dl;
+};
+
+__device__ __forceinline__ SearchOut write_certificate(const StepArgs &a, const SceneParams &sp, int gi,
+                                                       const Top3 &t, float L)
+{
+    SearchOut o = {0, 0, 0, 0.0};
+    const int n1 = (t.j0 != 0x7fffffff) ? t.j0 - sp.pt_off : -1;
+    const int n2 = (t.j1 != 0x7fffffff) ? t.j1 - sp.pt_off : -1;
+    if (a.mode == MODE_STEP) {
+        o.changed = n1 != a.nn[gi];
+        a.failed[gi] = (uint8_t)o.changed;
+        if (o.changed) {
+            o.missed = !a.inF[gi];
+            const int old = atomicAdd(&a.hfail[sp.h_off + a.hcell[gi]], 1);
+            o.first = old == 0;
+            o.dl = nlogn_step(a.nlogn, old);
+        }
+    }
+    a.nn[gi] = n1;
+    a.nn2[gi] = n2;
+    a.d1sq[gi] = t.d0;
+    a.d2sq[gi] = t.d1;
+    a.L[gi] = L;
+    return o;
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_search(const StepArgs a)
 {
+    constexpr int NR = (DIM == 3) ? 9 : 3;
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ int s_list[kSearchChunk];
+    __shared__ int2 s_rng[NR * kThreads];      // per-thread row ranges, column-major
     const int my = blockIdx.x * kSearchChunk + threadIdx.x;
     const uint32_t f = (my < a.n_total) ? (uint32_t)a.sflag[my] : 0u;
     uint32_t count;
@@ -564,19 +678,24 @@ __global__ void __launch_bounds__(kThreads) k_search(const StepArgs a)
     if (f) s_list[pre] = my;
     __syncthreads();
     if ((int)(threadIdx.x & ~31u) >= (int)count) return;  // whole idle warps leave together
+
     const bool active = threadIdx.x < count;
-    int s = -1, changed = 0, missed = 0, first = 0;
-    double dl = 0.0;
+    const int lane = threadIdx.x & 31;
+    int s = -1, gi = -1;
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    SearchOut o = {0, 0, 0, 0.0};
+    bool far = false;
     if (active) {
         const int slot = s_list[threadIdx.x];
-        const float4 q = a.sorted[slot];
-        int gi = __float_as_int(q.w);
+        q = a.sorted[slot];
+        gi = __float_as_int(q.w);
         if ((unsigned)gi >= (unsigned)a.n_total) {  // only after a timed-out scan
             atomicOr(a.status, ST_TIMEOUT);
             gi = slot;
         }
         s = a.scene_of[gi];
         const SceneParams sp = a.sp[s];
+        const SceneState &st = a.st[s];
         SearchCtx c;
         c.sorted = a.sorted;
         c.bstart = a.bucket_start;
@@ -587,36 +706,46 @@ __global__ void __launch_bounds__(kThreads) k_search(const StepArgs a)
         c.boff = sp.bucket_off;
         c.T = sp.bucket_mask + 1;
         c.mask = (uint32_t)sp.bucket_mask;
-        c.g = a.st[s].g_cur;
+        c.g = st.g_cur;
+        c.inv_g = st.inv_g;
+        c.dense = grid_is_dense<DIM>(c.g, c.T);
         Top3 t;
         float L;
-        grid_search<DIM>(c, t, L);
-        const int n1 = (t.j0 != 0x7fffffff) ? t.j0 - sp.pt_off : -1;
-        const int n2 = (t.j1 != 0x7fffffff) ? t.j1 - sp.pt_off : -1;
-        if (a.mode == MODE_STEP) {
-            changed = n1 != a.nn[gi];
-            a.failed[gi] = (uint8_t)changed;
-            if (changed) {
-                missed = !a.inF[gi];
-                const int old = atomicAdd(&a.hfail[sp.h_off + a.hcell[gi]], 1);
-                first = old == 0;
-                dl = nlogn_step(a.nlogn, old);
-            }
+        if (grid_search<DIM>(c, t, L, s_rng + threadIdx.x))
+            o = write_certificate(a, sp, gi, t, L);
+        else
+            far = true;
+    }
+    // Far queries (box would grow beyond kMaxExtend layers): the whole warp
+    // scans the query's scene with coalesced loads and merges its top-3.
+    unsigned farmask = __ballot_sync(kFull, far);
+    while (farmask) {
+        const int l = __ffs(farmask) - 1;
+        farmask &= farmask - 1;
+        const int fgi = __shfl_sync(kFull, gi, l);
+        const int fs = __shfl_sync(kFull, s, l);
+        const float4 fq = make_float4(__shfl_sync(kFull, q.x, l), __shfl_sync(kFull, q.y, l),
+                                      __shfl_sync(kFull, q.z, l), 0.0f);
+        const SceneParams sp = a.sp[fs];
+        Top3 t;
+        top3_reset(t);
+        for (int j = sp.pt_off + lane; j < sp.pt_off + sp.n; j += 32) {
+            const float4 cj = a.sorted[j];
+            const int jj = __float_as_int(cj.w);
+            const float D = sqdist<DIM>(fq, cj);
+            if (D <= t.d2 && jj != fgi) top3_insert(t, D, jj);
         }
-        a.nn[gi] = n1;
-        a.nn2[gi] = n2;
-        a.d1sq[gi] = t.d0;
-        a.d2sq[gi] = t.d1;
-        a.L[gi] = L;
+        warp_merge_top3(t);
+        if (lane == l) o = write_certificate(a, sp, gi, t, sqrt_lower(t.d2));
     }
     if (a.mode != MODE_STEP) return;
     // slots of one scene are contiguous, so lanes form contiguous scene runs
     const unsigned m = scene_run_mask(s);
     const int nsr = run_sum_i32(m, active ? 1 : 0);
-    const int nc = run_sum_i32(m, changed);
-    const int nm = run_sum_i32(m, missed);
-    const int fc = run_sum_i32(m, first);
-    const double sd = run_sum_f64(m, dl);
+    const int nc = run_sum_i32(m, o.changed);
+    const int nm = run_sum_i32(m, o.missed);
+    const int fc = run_sum_i32(m, o.first);
+    const double sd = run_sum_f64(m, o.dl);
     if (s >= 0 && run_leader(m)) {
         atomicAdd(&a.acc[s].n_searched, nsr);
         if (nc) {
@@ -672,6 +801,7 @@ __global__ void k_finalize(const StepArgs a)
         st.prev_nfront = nF;
     }
     st.g_cur = st.g_next;
+    st.inv_g = __frcp_rn((float)st.g_cur);
     a.st[s] = st;
 }
 

@@ -83,3 +83,15 @@ def test_struct_layouts_match_header():
     # cert_scene_result: 2 doubles + 16 four-byte fields
     assert ctypes.sizeof(cert.cert_scene_result) == 16 + 16 * 4
     assert ctypes.sizeof(cert.cert_config) == 4 + 4 + 8 + 8 + 4 + 4 + 16
+
+
+def test_python_modules_import_without_gpu():
+    import importlib
+    for name in ["paper_2606_18314_b300.cert", "paper_2606_18314_b300.selector", "paper_2606_18314_b300.scenes",
+                 "paper_2606_18314_b300.build"]:
+        importlib.import_module(name)
+    from paper_2606_18314_b300 import selector
+    p = selector.he_init(0)
+    assert p.shape == (4866,) and p.dtype.name == "float32"
+    assert abs(float(p[:512].std()) - (2.0 / 8) ** 0.5) < 0.1     # He-normal fan-in 8
+    assert float(abs(p[512:576]).max()) == 0.0                       # zero biases

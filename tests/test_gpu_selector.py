@@ -1,0 +1,212 @@
+"""GPU tests of the selector stack and the tuning entry points.
+
+* cert_mlp_forward / cert_mlp_grad / cert_mlp_adam against the FP64 oracle
+  (oracle/mlp.py): FP32 kernels, so agreement within 1e-4 relative.
+* the eight step features against the oracle's step quantities.
+* snapshot/restore, autotune, the THRESHOLD policy and the learned AUTO
+  schedule never change a certificate (bit-exact against the oracle).
+* the trainer learns a known decision rule from synthetic labels.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_2606_18314_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    from paper_2606_18314_b300 import build
+    build.build()
+    return t
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def normalised(X, norm):
+    return (X.astype(np.float64) - norm[:8]) * norm[8:]
+
+
+def test_mlp_forward_and_gradient_match_fp64_oracle(torch):
+    from paper_2606_18314_b300 import cert, selector
+    rng = np.random.default_rng(0)
+    n = 300                                       # several 64-row tiles and a ragged tail
+    X = (rng.standard_normal((n, 8)) * 3 + 1).astype(np.float32)
+    T = rng.standard_normal((n, 2)).astype(np.float32)
+    params = selector.he_init(3)
+    norm = selector.normalisation(X)
+    Xn = normalised(X, norm)
+    # forward
+    Y = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    cert.cert_mlp_forward(dev(torch, params), dev(torch, norm), dev(torch, X), Y)
+    Yref, _ = omlp.forward(params.astype(np.float64), Xn)
+    np.testing.assert_allclose(Y.cpu().numpy(), Yref, rtol=1e-4, atol=1e-4)
+    # gradient and loss
+    g = torch.zeros(omlp.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    work = torch.empty(cert.cert_mlp_workspace_bytes(n) // 4 + 1, dtype=torch.float32, device="cuda")
+    cert.cert_mlp_grad(dev(torch, params), dev(torch, norm), dev(torch, X), dev(torch, T), g, loss, work)
+    Lref, gref = omlp.grad(params.astype(np.float64), Xn, T.astype(np.float64))
+    assert abs(float(loss.item()) - Lref) <= 1e-4 * max(1.0, Lref)
+    gg = g.cpu().numpy()
+    scale = np.abs(gref).max()
+    assert np.max(np.abs(gg - gref)) <= 1e-4 * scale
+    # deterministic: the same call gives the same bits
+    g2 = torch.zeros_like(g)
+    cert.cert_mlp_grad(dev(torch, params), dev(torch, norm), dev(torch, X), dev(torch, T), g2, None, work)
+    assert torch.equal(g, g2)
+
+
+def test_adam_matches_oracle(torch):
+    from paper_2606_18314_b300 import cert, selector
+    rng = np.random.default_rng(1)
+    p = selector.he_init(4)
+    gr = rng.standard_normal(omlp.N_PARAMS).astype(np.float32)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    pd, gd, md, vd = dev(torch, p.copy()), dev(torch, gr), dev(torch, m), dev(torch, v)
+    for t in (1, 2, 3):
+        cert.cert_mlp_adam(pd, gd, md, vd, t, lr=1e-3)
+    pr, mr, vr = p.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for t in (1, 2, 3):
+        pr, mr, vr = omlp.adam(pr, gr.astype(np.float64), mr, vr, t, lr=1e-3)
+    np.testing.assert_allclose(pd.cpu().numpy(), pr, rtol=1e-5, atol=1e-6)
+
+
+def test_trainer_learns_a_known_rule(torch):
+    """Synthetic labels: incremental costs grow with the frontier fraction,
+    rebuild is flat, so the best choice is f0 < 0.4.  The trained network
+    must recover the rule and beat both plain policies on held-out rows."""
+    from paper_2606_18314_b300 import selector
+    rng = np.random.default_rng(2)
+    n = 6000
+    X = rng.random((n, 8)).astype(np.float32)
+    X[:, 3] = 3.0
+    t_inc = 0.2 + 2.0 * X[:, 0]
+    t_reb = np.full(n, 1.0)
+    T = np.log(np.stack([t_inc, t_reb], 1)).astype(np.float32)
+    tr, va = np.arange(5000), np.arange(5000, n)
+    trn = selector.Trainer(X[tr], T[tr], seed=1, batch=512)
+    hist = trn.fit(epochs=40, lr=3e-3)
+    assert hist[-1] < 0.05 * hist[0]
+    Y = selector.predict(trn.params_np(), trn.norm_np, X[va])
+    choose = Y[:, 0] <= Y[:, 1]
+    assert np.mean(choose == (X[va, 0] < 0.4)) > 0.95
+    r_learned = selector.regret(T[va], choose)
+    assert r_learned < 0.5 * selector.regret(T[va], np.ones(len(va), bool))
+    assert r_learned < 0.5 * selector.regret(T[va], np.zeros(len(va), bool))
+
+
+def test_features_match_oracle(torch):
+    from paper_2606_18314_b300 import cert
+    m = scenes.Motion("clustered_drift", 3000, 3, 2e-3, seed=8)
+    p = m.frame()
+    ctx = cert.Context(dev(torch, p))
+    ref = oracle.top2(p)
+    prev = None
+    for t in range(4):
+        q = m.advance()
+        ctx.step(dev(torch, q), 2e-3, "incremental")
+        f = ctx.features()[0]
+        r = oracle.step(p, q, ref)
+        n = q.shape[0]
+        assert f[0] == np.float32(len(r.frontier)) / np.float32(n)
+        assert abs(f[1] - r.H_cand) <= 1e-6
+        assert abs(f[2] - math.log(n)) <= 1e-6 * math.log(n)
+        assert f[3] == 3.0
+        want5 = math.log1p(min(float(r.eps_t) / max(float(r.med_c), 1e-30), 1e6))
+        assert abs(f[4] - want5) <= 1e-5 * max(1.0, want5)
+        assert abs(f[5] - r.m_cand / r.C) <= 1e-6
+        if prev is not None:
+            assert f[6] == np.float32(prev.n_failed) / np.float32(max(1, len(prev.frontier)))
+        assert f[7] == 0.0          # no selector loaded: no previous prediction
+        p, ref, prev = q, r.cert, r
+
+
+def assert_exact(ctx, pts_ref, lo=0, hi=None):
+    v = ctx.views()
+    hi = len(pts_ref.nn) if hi is None else hi
+    assert np.array_equal(v["nn"][lo:hi].cpu().numpy(), pts_ref.nn)
+    assert np.array_equal(v["d1sq"][lo:hi].cpu().numpy().view(np.uint32), pts_ref.d1sq.view(np.uint32))
+    assert np.array_equal(v["d2sq"][lo:hi].cpu().numpy().view(np.uint32), pts_ref.d2sq.view(np.uint32))
+
+
+def test_snapshot_restore_gives_identical_results(torch):
+    from paper_2606_18314_b300 import cert
+    m = scenes.Motion("ring_rotation", 4000, 3, 1e-3, seed=3)
+    fr = m.frames(3)
+    ctx = cert.Context(dev(torch, fr[0]))
+    ctx.step(dev(torch, fr[1]), 1e-3, "incremental")
+    ctx.snapshot()
+    ctx.step(dev(torch, fr[2]), 1e-3, "rebuild")
+    a = {k: v.clone() for k, v in ctx.views().items()}
+    res_a, _ = ctx.sync()
+    ctx.restore()
+    ctx.step(dev(torch, fr[2]), 1e-3, "incremental")
+    b = ctx.views()
+    res_b, _ = ctx.sync()
+    for k in ("nn", "d1sq", "d2sq", "cell", "failed"):
+        assert torch.equal(a[k], b[k]), k
+    assert res_a["n_failed"][0] == res_b["n_failed"][0] and res_a["n_frontier"][0] == res_b["n_frontier"][0]
+    assert_exact(ctx, oracle.top2(fr[2]))
+    with pytest.raises(cert.CertError):
+        ctx2 = cert.Context(dev(torch, fr[0]))
+        ctx2.restore()
+
+
+def test_autotune_and_cell_scales_keep_results_exact(torch):
+    from paper_2606_18314_b300 import cert
+    m = scenes.Motion("adversarial_crossing", 5000, 3, 1e-3, seed=4, steps=40)
+    fr = m.frames(12)
+    ctx = cert.Context(dev(torch, fr[0]))
+    ctx.step(dev(torch, fr[1]), 1e-3, "incremental")
+    scales = (0.75, 1.5, 3.0)
+    best, ms = ctx.autotune(dev(torch, fr[2:8]), 1e-3, "incremental", scales)
+    assert best in scales and np.all(ms > 0)
+    assert ctx.cell_scale() == best
+    assert_exact(ctx, oracle.top2(fr[1]))          # the tuner restored the state
+    for k, sc in zip(range(2, 12), (0.5, 4.0, 1.0, 0.8, 2.2, 1.5, 3.3, 0.6, 1.1, 1.9)):
+        ctx.set_cell_scale(sc)
+        ctx.step(dev(torch, fr[k]), 1e-3, "incremental")
+        ctx.sync()
+        assert_exact(ctx, oracle.top2(fr[k]))
+    with pytest.raises(cert.CertError):
+        ctx.set_cell_scale(0.0)
+
+
+def test_threshold_and_learned_schedules_are_exact(torch):
+    from paper_2606_18314_b300 import cert, selector
+    bm = scenes.BatchMotion.mixed(n_scenes=10, lo=400, hi=3000, eps=2e-3, seed=9)
+    off = bm.offsets
+    fr = bm.frames(5)
+    ctx = cert.Context(dev(torch, fr[0]), offsets=off)
+    params = selector.he_init(5)
+    norm = np.concatenate([np.zeros(8), np.ones(8)]).astype(np.float32)
+    for k, strat in zip(range(1, 6), ["threshold", "auto", "threshold", "auto", "auto"]):
+        if k == 2:
+            ctx.load_selector(params, norm)
+        ctx.step(dev(torch, fr[k]), 2e-3, strat)
+        res, _ = ctx.sync()
+        feats = ctx.features()
+        for s in range(10):
+            assert_exact(ctx, oracle.top2(fr[k][off[s]:off[s + 1]]), off[s], off[s + 1])
+            if strat == "threshold":
+                want = cert.CERT_INCREMENTAL if feats[s, 0] < 1.0 / feats[s, 2] else cert.CERT_REBUILD
+                assert res["strategy"][s] == want
+            else:
+                pi, pr = res["pred_inc"][s], res["pred_reb"][s]
+                assert res["strategy"][s] == (cert.CERT_INCREMENTAL if pi <= pr else cert.CERT_REBUILD)
+        if strat == "auto":
+            # the in-loop inference equals the batch inference kernel on the same features
+            Y = selector.predict(params, norm, feats)
+            np.testing.assert_allclose(np.stack([res["pred_inc"], res["pred_reb"]], 1), Y, rtol=1e-4, atol=1e-4)
+    ctx.load_selector(None, None)
