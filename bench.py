@@ -37,7 +37,7 @@ from paper_2606_18314_b300 import scenes  # noqa: E402
 
 METRIC = "certified point-updates/s"
 UNIT = "point-updates/s"
-KERNELS_PER_STEP = 6
+KERNELS_PER_STEP = 7   # prepare, scan, select, scatter_refresh, search, far, finalize
 
 # Per-phase algorithmic (compulsory DRAM) bytes, see DESIGN.md "Roofline".
 #   prepare: read p' (4 dim) + p (16), write packed p' (16), (bucket, rank) (8), cell (4),
@@ -126,9 +126,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_workload(name, rank, frames, n_scenes=512):
+def make_workload(name, rank, frames, n_scenes=512, family=None):
     if name == "batched":
         bm = scenes.BatchMotion.mixed(n_scenes=n_scenes, dim=3, eps=1e-3, seed=4 + 1000 * rank, steps=100)
+        if family:   # diagnostics: every scene of one family (same sizes and seeds)
+            bm = scenes.BatchMotion([scenes.Motion(family, m.n, 3, 1e-3, seed=m.seed, steps=100)
+                                     for m in bm.scenes])
         return bm.frames(frames), bm.offsets, 1e-3, {
             "workload": f"batched-{n_scenes}-scenes", "scenes": n_scenes, "n_range": [500, 16000], "dim": 3,
             "eps": 1e-3,
@@ -217,6 +220,42 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def graph_loop(ctx, dev_frames, F, eps, strategy, K, use_graph, stream, torch):
+    """Time K steps from the start of the ping-pong cycle (state at frame 0);
+    the cycle (2F steps, even) is captured once as a CUDA graph and replayed.
+    Returns (ms, steps taken)."""
+    C = 2 * F
+    graphs = []
+    if use_graph:
+        full, rem = divmod(K, C)
+        if full:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                for k in range(C):
+                    ctx.step(dev_frames[cycle_index(k, F)], eps, strategy)
+            graphs.append((g, full))
+        if rem:
+            g2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g2):
+                for k in range(rem):
+                    ctx.step(dev_frames[cycle_index(k, F)], eps, strategy)
+            graphs.append((g2, 1))
+        torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    if graphs:
+        for g, reps in graphs:
+            for _ in range(reps):
+                g.replay()
+    else:
+        for k in range(K):
+            ctx.step(dev_frames[cycle_index(k, F)], eps, strategy)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), K
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -224,14 +263,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=64)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "c1", "c2", "c3"])
-    ap.add_argument("--strategy", default="incremental", choices=["auto", "incremental", "rebuild", "allpairs"])
+    ap.add_argument("--strategy", default="auto",
+                    choices=["auto", "incremental", "rebuild", "allpairs", "threshold"])
     ap.add_argument("--frames", type=int, default=32)
     ap.add_argument("--scenes", type=int, default=512, help="scenes in the batched workload")
+    ap.add_argument("--family", default=None, choices=list(scenes.FAMILIES), help="diagnostics: one family only")
+    ap.add_argument("--cell-scale", type=float, default=0.0, help="search-grid cell side / reference d2 (0: default)")
+    ap.add_argument("--cell-quantile", type=float, default=0.0, help="d2 quantile of the reference (0: default)")
+    ap.add_argument("--bucket-factor", type=int, default=0, help="hashed buckets per scene / next_pow2(n)")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--prof-steps", type=int, default=200)
+    ap.add_argument("--regret-steps", type=int, default=32)
+    ap.add_argument("--compare-steps", type=int, default=256)
+    ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--compare", action="store_true", help="also time the other plain strategies")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -243,7 +290,7 @@ def main():
 
     import torch
     from paper_2606_18314_b300 import build as cbuild
-    from paper_2606_18314_b300 import cert
+    from paper_2606_18314_b300 import cert, selector
     cbuild.build()
     torch.cuda.set_device(local)
     dist = None
@@ -252,15 +299,19 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     F = max(2, args.frames)
-    frames, offsets, eps, cfg = make_workload(args.workload, rank, F, args.scenes)
+    C = 2 * F
+    frames, offsets, eps, cfg = make_workload(args.workload, rank, F, args.scenes, args.family)
+    if args.family:
+        cfg = dict(cfg, families=[args.family])
     N, dim = frames.shape[1], frames.shape[2]
     S = len(offsets) - 1
     dev_frames = torch.from_numpy(frames).cuda()
     strat = cert.STRATEGY[args.strategy]
     stream = torch.cuda.current_stream()
+    use_graph = not args.no_graph
 
-    ctx = cert.Context(dev_frames[0], offsets=offsets)
-    C = 2 * F
+    ctx = cert.Context(dev_frames[0], offsets=offsets, cell_scale=args.cell_scale, cell_quantile=args.cell_quantile,
+                       bucket_factor=args.bucket_factor)
     clock = [0]   # steps taken along the ping-pong cycle; the state sits at frame cycle_index(clock-1)
 
     def do_step(strategy=strat):
@@ -271,53 +322,44 @@ def main():
         while clock[0] % C:
             do_step(strategy)
 
-    # warm-up: W eager steps, then complete the cycle so the graph starts at frame 0
-    W = max(3, args.warmup)
-    W = int(math.ceil(W / C) * C)
+    sel_meta = None
+    if args.strategy == "auto":
+        if not os.path.exists(selector.WEIGHTS):
+            raise SystemExit(f"selector weights missing ({selector.WEIGHTS}); "
+                             "run python -m paper_2606_18314_b300.selector collect/train")
+        params, norm = selector.load()
+        ctx.load_selector(params, norm)
+        sel_meta = json.loads(str(np.load(selector.WEIGHTS)["meta"]))
+
+    # warm-up: W eager steps (whole cycles), the autotuner on the next 8 frames, back to frame 0
+    W = int(math.ceil(max(3, args.warmup) / C) * C)
     for _ in range(W):
         do_step()
+    tuned = None
+    if not args.no_autotune:
+        idx = [cycle_index(clock[0] + k, F) for k in range(min(8, C))]
+        probe = torch.stack([dev_frames[i] for i in idx]).contiguous()
+        scales = (1.5, 2.0, 2.5, 3.0, 4.0)
+        best, ms_sc = ctx.autotune(probe, eps, strat if strat != cert.CERT_ALLPAIRS else cert.CERT_INCREMENTAL,
+                                   scales)
+        tuned = {"scales": list(scales), "ms": [float(x) for x in ms_sc], "best": best}
+        del probe
+    to_cycle_start()
     torch.cuda.synchronize()
-    ctx.sync()
+    ctx.sync(raise_on_status=False)
 
+    # ---- the timed region: K steps of the chosen strategy
     K = args.steps
-    graphs = []
-    if not args.no_graph:
-        full, rem = divmod(K, C)
-        if full:
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                for k in range(C):
-                    ctx.step(dev_frames[cycle_index(k, F)], eps, strat)
-            graphs.append((g, full))
-        if rem:
-            g2 = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g2):
-                for k in range(rem):
-                    ctx.step(dev_frames[cycle_index(k, F)], eps, strat)
-            graphs.append((g2, 1))
-        torch.cuda.synchronize()
-
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    if graphs:
-        for g, reps in graphs:
-            for _ in range(reps):
-                g.replay()
-    else:
-        for k in range(K):
-            do_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, _ = graph_loop(ctx, dev_frames, F, eps, strat, K, use_graph, stream, torch)
+    clock[0] += K
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
     res, rc = ctx.sync(raise_on_status=False)
     assert int(res["n_missed"].sum()) == 0, "safety rule missed a failure"
     ms_max = ms
@@ -330,11 +372,56 @@ def main():
         dist.all_reduce(nt)
         n_all = int(nt.item())
     value = n_all * K / (ms_max / 1e3)
-
-    if graphs:
-        clock[0] += K          # the replays advanced the state by K steps
     to_cycle_start()
-    torch.cuda.synchronize()
+
+    # ---- the same batch under each plain strategy, and the plain single-scene loops
+    compare = {}
+    if not args.no_compare:
+        Kc = max(1, min(K, args.compare_steps))
+        for name in ["incremental", "rebuild", "threshold", "auto"]:
+            if name == "auto" and sel_meta is None:
+                continue
+            torch.cuda.synchronize()
+            msc, _ = graph_loop(ctx, dev_frames, F, eps, cert.STRATEGY[name], Kc, use_graph, stream, torch)
+            clock[0] += Kc
+            to_cycle_start(cert.STRATEGY[name])
+            compare[f"batched_{name}"] = N * Kc / (msc / 1e3)
+        if args.workload == "batched":
+            m2 = scenes.Motion("uniform_brownian", 16000, 3, 1e-3, seed=1 + rank, steps=200)
+            f2 = torch.from_numpy(m2.frames(F)).cuda()
+            for name in ["incremental", "rebuild"]:
+                c2 = cert.Context(f2[0], cell_scale=ctx.cell_scale())
+                for k in range(C):
+                    c2.step(f2[cycle_index(k, F)], 1e-3, cert.STRATEGY[name])
+                msc, _ = graph_loop(c2, f2, F, 1e-3, cert.STRATEGY[name], max(C, min(K, 4 * C)), use_graph,
+                                    stream, torch)
+                compare[f"plain_16000_d3_{name}"] = 16000 * max(C, min(K, 4 * C)) / (msc / 1e3)
+                c2.close()
+            del f2
+
+    # ---- regret against the per-step measured best, from identical state
+    regret = None
+    if args.regret_steps > 0 and sel_meta is not None:
+        names = ["incremental", "rebuild", "threshold", "auto"]
+        tim = {n: [] for n in names}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(args.regret_steps):
+            ctx.snapshot()
+            for j, name in enumerate(names):
+                if j:
+                    ctx.restore()
+                e0.record(stream)
+                ctx.step(dev_frames[cycle_index(clock[0], F)], eps, cert.STRATEGY[name])
+                e1.record(stream)
+                e1.synchronize()
+                tim[name].append(e0.elapsed_time(e1))
+            clock[0] += 1
+        t = {n: np.array(v) for n, v in tim.items()}
+        best = np.minimum(t["incremental"], t["rebuild"])
+        regret = {n: float((t[n] - best).sum() / best.sum()) for n in names}
+        regret["steps"] = args.regret_steps
+        regret["reference"] = "per step min(incremental, rebuild) on identical state, CUDA events"
+        to_cycle_start()
 
     # ---- per-phase timing (CUDA events on the launching stream), same workload, eager
     P = max(1, args.prof_steps)
@@ -347,11 +434,11 @@ def main():
     prof = ctx.profile_end()
     mean_ms = prof.mean(axis=0)
     peaks, peak_kind = load_peaks()
-    n_buckets = int(sum(1 << int(math.ceil(math.log2(max(int(n), 16)))) for n in np.diff(offsets)))
-    zero_bytes = 0
+    n_buckets = int(sum(1 << int(math.ceil(math.log2(max(int(n), 16)))) for n in np.diff(offsets))) * \
+        max(1, args.bucket_factor)
     per_phase = {}
     for j, ph in enumerate(PHASES):
-        byts = [phase_bytes(ph, N, dim, n_buckets, c[0], c[1], zero_bytes) for c in counts]
+        byts = [phase_bytes(ph, N, dim, n_buckets, c[0], c[1], 0) for c in counts]
         gbs = [b / (t * 1e-3) / 1e9 for b, t in zip(byts, prof[:, j]) if t > 0]
         per_phase[ph] = {"ms": float(mean_ms[j]), "share": float(mean_ms[j] / mean_ms.sum()),
                          "bytes": float(np.mean(byts)), "gbs": float(np.mean(gbs)) if gbs else 0.0}
@@ -365,6 +452,7 @@ def main():
                 "phases": per_phase}
 
     # ---- end to end through the public API with host buffers (pinned), per step H2D + D2H
+    to_cycle_start()
     E = max(1, min(args.e2e_steps, K))
     host_frames = torch.from_numpy(frames).pin_memory()
     out = np.zeros(S, cert.SCENE_DTYPE)
@@ -379,40 +467,25 @@ def main():
     e2e = {"value": N * E / el * (n_all / N), "unit": UNIT, "h2d_bytes_per_step": row_bytes,
            "d2h_bytes_per_step": int(S * cert.SCENE_DTYPE.itemsize), "steps": E}
 
-    compare = {}
-    if args.compare:
-        for other in ["incremental", "rebuild"]:
-            if other == args.strategy:
-                continue
-            so = cert.STRATEGY[other]
-            to_cycle_start(so)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for k in range(C):
-                do_step(so)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            compare[other] = N * C / (e0.elapsed_time(e1) / 1e3)
-        compare[args.strategy + " (timed above)"] = value
-
     cb = None
     if rank == 0 and args.cpu_seconds > 0:
         cb, _, _ = cpu_baseline(frames, offsets, dim, budget_s=args.cpu_seconds)
 
     if rank == 0:
         cfg = dict(cfg)
-        cfg.update({"strategy": args.strategy, "graph": not args.no_graph, "frames": F + 1,
+        cfg.update({"strategy": args.strategy, "graph": use_graph, "frames": F + 1,
+                    "cell_scale": ctx.cell_scale(), "autotune": tuned,
                     "motion": "ping-pong over pre-generated frames, every step <= eps",
                     "l2": "no flush: working set > 126 MB L2 (inputs larger than L2)",
                     "parallelism": f"scene-replicas x{world}"})
+        if sel_meta is not None:
+            cfg["selector"] = {k: sel_meta[k] for k in sel_meta if k.startswith(("rows", "val_"))}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
-                "step_counts": step_counts,
+                "step_counts": step_counts, "compare": compare, "regret": regret,
                 "status": cert.STATUS_NAMES[rc] if 0 <= rc < len(cert.STATUS_NAMES) else rc}
-        if compare:
-            line["compare"] = compare
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

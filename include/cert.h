@@ -69,9 +69,13 @@ typedef struct {
                                  increasing, every scene >= 3 points, total < 2^31;
                                  NULL allowed when n_scenes == 1 together with n_total */
     int64_t n_total;          /* total points (used when offsets == NULL)             */
-    float cell_scale;         /* search-grid cell side / median d2 (0 -> 1.5)         */
+    float cell_scale;         /* search-grid cell side / reference d2 (0 -> 2.5)      */
     int32_t policy;           /* strategy for CERT_AUTO without a selector (0 -> INCREMENTAL) */
-    int32_t reserved[4];      /* must be zero                                          */
+    int32_t bucket_factor;    /* hashed-grid buckets per scene = factor x next_pow2(n);
+                                 1, 2, 4 or 8 (0 -> 1)                                 */
+    float cell_quantile;      /* reference d2 = this quantile of a scene's previous d2
+                                 over its first min(n,1024) points, in (0,1] (0 -> 0.5) */
+    int32_t reserved[2];      /* must be zero                                          */
 } cert_config;
 
 /* Per-scene scalars of the last step.  Same layout on device and host. */
@@ -159,10 +163,14 @@ cert_status cert_distances(cert_ctx *ctx, float *d_d1, float *d_d2, void *stream
 cert_status cert_allpairs(const float *d_pos, int64_t n, int32_t dim, const int32_t *d_queries,
                           int64_t nq, int32_t *d_nn, float *d_d1sq, float *d_d2sq, void *stream);
 
-/* Search-grid cell side of every scene = scale x (truncated median d2 of the
- * scene's previous certificates); takes effect from the next step.  Only the
+/* Search-grid cell side of every scene = scale x (reference d2 of the
+ * scene's previous certificates, see cell_quantile); takes effect from the
+ * next step.  Only the
  * speed depends on it: certificates are exact for any scale > 0. */
 cert_status cert_set_cell_scale(cert_ctx *ctx, float scale);
+/* Quantile of the previous d2 (over the first min(n,1024) points, truncated
+ * to 3 mantissa bits) that the cell side is a multiple of; in (0, 1]. */
+cert_status cert_set_cell_quantile(cert_ctx *ctx, float quantile);
 float cert_get_cell_scale(const cert_ctx *ctx);
 
 /* Autotuner (the grid cell side of Sec. 2's uniform grid, chosen by timing):

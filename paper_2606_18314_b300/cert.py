@@ -29,7 +29,8 @@ class cert_config(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("n_scenes", ctypes.c_int32),
                 ("offsets", ctypes.POINTER(ctypes.c_int64)), ("n_total", ctypes.c_int64),
                 ("cell_scale", ctypes.c_float), ("policy", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("bucket_factor", ctypes.c_int32), ("cell_quantile", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class cert_scene_result(ctypes.Structure):
@@ -66,7 +67,7 @@ _lib = None
 EXPORTS = ["cert_init", "cert_step", "cert_step_host", "cert_rebuild", "cert_get_views",
            "cert_sync_result", "cert_distances", "cert_allpairs", "cert_destroy", "cert_last_error",
            "cert_version", "cert_profile_begin", "cert_profile_end",
-           "cert_allpairs_noalloc", "cert_set_cell_scale", "cert_get_cell_scale", "cert_autotune",
+           "cert_allpairs_noalloc", "cert_set_cell_scale", "cert_set_cell_quantile", "cert_get_cell_scale", "cert_autotune",
            "cert_snapshot", "cert_restore", "cert_get_features", "cert_selector_load",
            "cert_mlp_workspace_bytes", "cert_mlp_forward", "cert_mlp_grad", "cert_mlp_adam"]
 MLP_PARAMS = 4866
@@ -98,6 +99,8 @@ def lib():
     L.cert_version.argtypes = []
     L.cert_version.restype = ctypes.c_char_p
     L.cert_set_cell_scale.argtypes = [vp, f32]
+    L.cert_set_cell_quantile.argtypes = [vp, f32]
+    L.cert_set_cell_quantile.restype = ctypes.c_int
     L.cert_get_cell_scale.argtypes = [vp]
     L.cert_get_cell_scale.restype = f32
     L.cert_autotune.argtypes = [vp, vp, i64, i32, f32, i32, vp, i32, vp, vp, vp]
@@ -261,7 +264,8 @@ class Context:
     (valid until the next call); ``sync`` calls ``cert_sync_result``.
     """
 
-    def __init__(self, pos, offsets=None, cell_scale=0.0, policy=CERT_INCREMENTAL, stream=None):
+    def __init__(self, pos, offsets=None, cell_scale=0.0, policy=CERT_INCREMENTAL, stream=None,
+                 bucket_factor=0, cell_quantile=0.0):
         import torch
         self.dim = int(pos.shape[1])
         self._keep = []
@@ -276,6 +280,8 @@ class Context:
         cfg.n_total = int(offsets[-1])
         cfg.cell_scale = float(cell_scale)
         cfg.policy = int(policy)
+        cfg.bucket_factor = int(bucket_factor)
+        cfg.cell_quantile = float(cell_quantile)
         self.n_scenes = cfg.n_scenes
         self.n = cfg.n_total
         h = ctypes.c_void_p()
@@ -370,6 +376,9 @@ class Context:
     # ---- tuning, snapshots, selector -------------------------------------------------
     def set_cell_scale(self, scale):
         _check(lib().cert_set_cell_scale(self.h, float(scale)), self.h)
+
+    def set_cell_quantile(self, q):
+        _check(lib().cert_set_cell_quantile(self.h, float(q)), self.h)
 
     def cell_scale(self):
         return float(lib().cert_get_cell_scale(self.h))

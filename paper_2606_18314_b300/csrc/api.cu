@@ -20,7 +20,9 @@ using namespace certk;
 struct cert_ctx {
     int dim = 0, S = 0;
     int64_t N = 0;
-    float cell_scale = 1.5f;
+    float cell_scale = 2.5f;
+    float cell_quantile = 0.5f;
+    int bucket_factor = 1;
     int policy = STRAT_INC;
     std::vector<SceneParams> h_sp;
     int n_buckets = 0, n_buckets_pad = 0, ntiles_b = 0, ntiles_p = 0;
@@ -43,6 +45,7 @@ struct cert_ctx {
     int2 *brank = nullptr;
     float4 *sorted = nullptr;
     int32_t *bucket_start = nullptr;
+    int32_t *far_list = nullptr, *far_count = nullptr;
     double *nlogn = nullptr;
     float *stage = nullptr;
     APItem *ap_items = nullptr;
@@ -150,6 +153,8 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.brank = c->brank;
     a.sorted = c->sorted;
     a.sflag = c->sflag;
+    a.far_list = c->far_list;
+    a.far_count = c->far_count;
     a.nn = c->nn;
     a.nn2 = c->nn2;
     a.d1sq = c->d1sq;
@@ -172,6 +177,7 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.res = c->res;
     a.policy = c->policy;
     a.cell_scale = c->cell_scale;
+    a.cell_quantile = c->cell_quantile;
     a.sel_params = c->have_sel ? c->sel_params : nullptr;
     a.sel_norm = c->have_sel ? c->sel_norm : nullptr;
     a.feat = c->feat;
@@ -210,8 +216,13 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     if (!d_pos) return fail(nullptr, CERT_EINVAL, "positions are NULL");
     if (cfg->dim != 2 && cfg->dim != 3) return fail(nullptr, CERT_EINVAL, "dim must be 2 or 3");
     if (cfg->n_scenes < 1) return fail(nullptr, CERT_EINVAL, "n_scenes must be >= 1");
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 2; ++k)
         if (cfg->reserved[k]) return fail(nullptr, CERT_EINVAL, "reserved fields must be zero");
+    if (cfg->bucket_factor != 0 && cfg->bucket_factor != 1 && cfg->bucket_factor != 2 && cfg->bucket_factor != 4 &&
+        cfg->bucket_factor != 8)
+        return fail(nullptr, CERT_EINVAL, "bucket_factor must be 0, 1, 2, 4 or 8");
+    if (!(cfg->cell_quantile >= 0.0f && cfg->cell_quantile <= 1.0f))
+        return fail(nullptr, CERT_EINVAL, "cell_quantile must be in [0, 1]");
     if (!(cfg->cell_scale >= 0.0f) || !std::isfinite(cfg->cell_scale))
         return fail(nullptr, CERT_EINVAL, "cell_scale must be finite and >= 0");
     if (cfg->policy < 0 || cfg->policy > STRAT_REB)
@@ -232,7 +243,9 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->dim = cfg->dim;
     c->S = cfg->n_scenes;
     c->N = off.back();
-    c->cell_scale = cfg->cell_scale > 0.0f ? cfg->cell_scale : 1.5f;
+    c->cell_scale = cfg->cell_scale > 0.0f ? cfg->cell_scale : 2.5f;
+    c->cell_quantile = cfg->cell_quantile > 0.0f ? cfg->cell_quantile : 0.5f;
+    c->bucket_factor = cfg->bucket_factor > 0 ? cfg->bucket_factor : 1;
     c->policy = cfg->policy == STRAT_AUTO ? STRAT_INC : cfg->policy;
     cudaStream_t s = (cudaStream_t)stream;
 
@@ -248,7 +261,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
         const int64_t n = off[k + 1] - off[k];
         p.pt_off = (int32_t)off[k];
         p.n = (int32_t)n;
-        const int T = next_pow2(std::max<int64_t>(n, 16));
+        const int T = next_pow2(std::max<int64_t>(n, 16)) * c->bucket_factor;
         p.bucket_off = (int32_t)boff;
         p.bucket_mask = T - 1;
         boff += T;
@@ -284,13 +297,14 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_L = cv.take<float>(N), o_hcell = cv.take<int32_t>(N), o_front = cv.take<int32_t>(N),
                  o_inF = cv.take<uint8_t>(Npad), o_failed = cv.take<uint8_t>(Npad),
                  o_sflag = cv.take<uint8_t>(Npad), o_brank = cv.take<int2>(N), o_sorted = cv.take<float4>(N),
-                 o_bstart = cv.take<int32_t>(c->n_buckets_pad), o_nlogn = cv.take<double>(kNlognTable),
+                 o_bstart = cv.take<int32_t>(c->n_buckets_pad), o_far = cv.take<int32_t>(N),
+                 o_nlogn = cv.take<double>(kNlognTable),
                  o_stage = cv.take<float>(N * c->dim), o_items = cv.take<APItem>(items.size()),
                  o_pd = cv.take<float>(3 * apoff), o_pj = cv.take<int32_t>(3 * apoff),
                  o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16), o_feat = cv.take<float>(S * 8);
     cv.off = (cv.off + 255) & ~size_t(255);
     const size_t zero_begin = cv.off;
-    const size_t o_acc = cv.take<SceneAcc>(S), o_ctr = cv.take<uint32_t>(4),
+    const size_t o_acc = cv.take<SceneAcc>(S), o_ctr = cv.take<uint32_t>(4), o_farc = cv.take<int32_t>(4),
                  o_tb = cv.take<uint64_t>(c->ntiles_b), o_tp = cv.take<uint64_t>(c->ntiles_p),
                  o_bcount = cv.take<int32_t>(c->n_buckets_pad), o_hocc = cv.take<int32_t>(hoff),
                  o_hfail = cv.take<int32_t>(hoff), o_hcand = cv.take<int32_t>(hoff);
@@ -324,6 +338,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->brank = (int2 *)(b + o_brank);
     c->sorted = (float4 *)(b + o_sorted);
     c->bucket_start = (int32_t *)(b + o_bstart);
+    c->far_list = (int32_t *)(b + o_far);
+    c->far_count = (int32_t *)(b + o_farc);
     c->nlogn = (double *)(b + o_nlogn);
     c->stage = (float *)(b + o_stage);
     c->ap_items = (APItem *)(b + o_items);
@@ -554,6 +570,14 @@ cert_status cert_set_cell_scale(cert_ctx *c, float scale)
 }
 
 float cert_get_cell_scale(const cert_ctx *c) { return c ? c->cell_scale : 0.0f; }
+
+cert_status cert_set_cell_quantile(cert_ctx *c, float q)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    if (!(q > 0.0f && q <= 1.0f)) return fail(c, CERT_EINVAL, "cell_quantile must be in (0, 1]");
+    c->cell_quantile = q;
+    return CERT_OK;
+}
 
 cert_status cert_get_features(cert_ctx *c, float *h_feat)
 {

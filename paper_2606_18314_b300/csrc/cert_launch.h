@@ -35,6 +35,8 @@ struct StepArgs {
     int2 *brank;                   // [n] (bucket, rank in bucket)
     float4 *sorted;                // [n] positions in bucket order, .w = point index bits
     uint8_t *sflag;                // [n_pad] by sorted slot: 1 = search this point
+    int32_t *far_list;             // [n] sorted slots left to the far pass
+    int32_t *far_count;            // number of entries in far_list (zeroed every call)
     // certificates
     int32_t *nn, *nn2;
     float *d1sq, *d2sq, *L;
@@ -51,6 +53,7 @@ struct StepArgs {
     float declared_eps;
     int strategy, policy;
     float cell_scale;
+    float cell_quantile;
     const float *sel_params;       // selector weights (NULL: none loaded)
     const float *sel_norm;         // feature mean[8], 1/std[8] (NULL: none loaded)
     float *feat;                   // [n_scenes][8] selector features of the last step

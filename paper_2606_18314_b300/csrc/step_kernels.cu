@@ -284,7 +284,9 @@ __global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
     bitonic_sort_1024(s_c);
     bitonic_sort_1024(s_d);
     const float med_c = __uint_as_float(s_c[(ns - 1) / 2] & 0xFFF00000u);
-    const float med_d2 = __uint_as_float(s_d[(ns - 1) / 2] & 0xFFF00000u);
+    // reference d2 for the search-grid cell side: a quantile of the sample
+    const int qi = min(ns - 1, max(0, (int)(a.cell_quantile * (float)(ns - 1))));
+    const float med_d2 = __uint_as_float(s_d[qi] & 0xFFF00000u);
 
     int strat = STRAT_INC;
     if (a.mode == MODE_STEP) {
@@ -522,8 +524,8 @@ constexpr float kFaceSlack = 0x1p-17f;   // >> FP error of cell assignment and f
 // that limits the enclosure -- until the runner-up is provably enclosed (its
 // distance is below the distance to every face that is not on the grid
 // edge; boundary cells are clamped and extend to infinity), as in Cor. A.2.
-// Returns false after kMaxExtend layers; such a query is finished by a whole
-// warp (far pass of k_search).
+// Returns false after kMaxExtend layers; such a query is appended to the far
+// list and finished by k_far.
 template <int DIM>
 __device__ __forceinline__ bool grid_search(const SearchCtx &c, Top3 &t, float &Lout, int2 *rng)
 {
@@ -684,7 +686,6 @@ __global__ void __launch_bounds__(kThreads) k_search(const StepArgs a)
     int s = -1, gi = -1;
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
     SearchOut o = {0, 0, 0, 0.0};
-    bool far = false;
     if (active) {
         const int slot = s_list[threadIdx.x];
         q = a.sorted[slot];
@@ -714,29 +715,7 @@ __global__ void __launch_bounds__(kThreads) k_search(const StepArgs a)
         if (grid_search<DIM>(c, t, L, s_rng + threadIdx.x))
             o = write_certificate(a, sp, gi, t, L);
         else
-            far = true;
-    }
-    // Far queries (box would grow beyond kMaxExtend layers): the whole warp
-    // scans the query's scene with coalesced loads and merges its top-3.
-    unsigned farmask = __ballot_sync(kFull, far);
-    while (farmask) {
-        const int l = __ffs(farmask) - 1;
-        farmask &= farmask - 1;
-        const int fgi = __shfl_sync(kFull, gi, l);
-        const int fs = __shfl_sync(kFull, s, l);
-        const float4 fq = make_float4(__shfl_sync(kFull, q.x, l), __shfl_sync(kFull, q.y, l),
-                                      __shfl_sync(kFull, q.z, l), 0.0f);
-        const SceneParams sp = a.sp[fs];
-        Top3 t;
-        top3_reset(t);
-        for (int j = sp.pt_off + lane; j < sp.pt_off + sp.n; j += 32) {
-            const float4 cj = a.sorted[j];
-            const int jj = __float_as_int(cj.w);
-            const float D = sqdist<DIM>(fq, cj);
-            if (D <= t.d2 && jj != fgi) top3_insert(t, D, jj);
-        }
-        warp_merge_top3(t);
-        if (lane == l) o = write_certificate(a, sp, gi, t, sqrt_lower(t.d2));
+            a.far_list[atomicAdd(a.far_count, 1)] = slot;   // finished by k_far
     }
     if (a.mode != MODE_STEP) return;
     // slots of one scene are contiguous, so lanes form contiguous scene runs
@@ -754,6 +733,73 @@ __global__ void __launch_bounds__(kThreads) k_search(const StepArgs a)
             atomicAdd(&a.acc[s].failed_cells, fc);
             atomicAdd(&a.acc[s].s_fail, sd);
         }
+    }
+}
+
+// ============================================================================ k_far
+
+// Queries whose box would grow beyond kMaxExtend layers (points far from
+// their neighbours relative to the scene's cell size).  One CTA per query
+// scans the whole scene with coalesced loads, four in flight per thread, and
+// merges the 256 partial top-3 lists; the result is exact (every point seen).
+constexpr int kFarCtas = 2 * 148;
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_far(const StepArgs a)
+{
+    __shared__ float s_d[kThreads / 32][3];
+    __shared__ int s_j[kThreads / 32][3];
+    const int nfar = *a.far_count;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int item = blockIdx.x; item < nfar; item += gridDim.x) {
+        const int slot = a.far_list[item];
+        const float4 q = a.sorted[slot];
+        int gi = __float_as_int(q.w);
+        if ((unsigned)gi >= (unsigned)a.n_total) gi = slot;
+        const int s = a.scene_of[gi];
+        const SceneParams sp = a.sp[s];
+        Top3 t;
+        top3_reset(t);
+        const int end = sp.pt_off + sp.n;
+        int j = sp.pt_off + threadIdx.x;
+        for (; j + 3 * kThreads < end; j += 4 * kThreads) {
+            float4 c[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) c[u] = a.sorted[j + u * kThreads];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int jj = __float_as_int(c[u].w);
+                const float D = sqdist<DIM>(q, c[u]);
+                if (D <= t.d2 && jj != gi) top3_insert(t, D, jj);
+            }
+        }
+        for (; j < end; j += kThreads) {
+            const float4 c = a.sorted[j];
+            const int jj = __float_as_int(c.w);
+            const float D = sqdist<DIM>(q, c);
+            if (D <= t.d2 && jj != gi) top3_insert(t, D, jj);
+        }
+        warp_merge_top3(t);
+        if (lane == 0) {
+            s_d[warp][0] = t.d0; s_d[warp][1] = t.d1; s_d[warp][2] = t.d2;
+            s_j[warp][0] = t.j0; s_j[warp][1] = t.j1; s_j[warp][2] = t.j2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Top3 r;
+            top3_reset(r);
+            for (int w = 0; w < kThreads / 32; ++w)
+                for (int k = 0; k < 3; ++k)
+                    if (s_j[w][k] != 0x7fffffff) top3_insert(r, s_d[w][k], s_j[w][k]);
+            const SearchOut o = write_certificate(a, sp, gi, r, sqrt_lower(r.d2));
+            if (a.mode == MODE_STEP && o.changed) {
+                atomicAdd(&a.acc[s].n_failed, 1);
+                atomicAdd(&a.acc[s].n_missed, o.missed);
+                atomicAdd(&a.acc[s].failed_cells, o.first);
+                atomicAdd(&a.acc[s].s_fail, o.dl);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -828,7 +874,10 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
     case PH_SCAN: k_scan<DIM><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a); break;
     case PH_SELECT: k_select<DIM><<<a.n_scenes, kThreads, 0, st>>>(a); break;
     case PH_SCATTER: k_scatter_refresh<DIM><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(a); break;
-    case PH_SEARCH: k_search<DIM><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a); break;
+    case PH_SEARCH:
+        k_search<DIM><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
+        if (cudaPeekAtLastError() == cudaSuccess) k_far<DIM><<<kFarCtas, kThreads, 0, st>>>(a);
+        break;
     case PH_FINALIZE: k_finalize<<<nblk(a.n_scenes, 128), 128, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
     }

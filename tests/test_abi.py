@@ -69,6 +69,12 @@ def test_host_argument_validation_without_gpu(L):
     cfg.reserved[0] = 1
     assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
     cfg.reserved[0] = 0
+    cfg.bucket_factor = 3
+    assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
+    cfg.bucket_factor = 0
+    cfg.cell_quantile = 1.5
+    assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
+    cfg.cell_quantile = 0.0
     cfg.policy = 3
     assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
     assert L.cert_step(None, None, ctypes.c_float(1e-3), 1, None, None) == cert.CERT_EINVAL
