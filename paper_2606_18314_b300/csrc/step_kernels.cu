@@ -206,61 +206,84 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     }
     __syncthreads();
     uint32_t run = s_excl + pre;
+    // a thread's 8 consecutive points nearly always share one scene: accumulate
+    // locally and reduce once per warp; a scene change inside the 8 is flushed directly
+    int cur = -1, acc_first = 0;
+    double acc_dl = 0.0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int i = base + k;
         const int s = sc[k];
-        int first = 0;
-        double dl = 0.0;
         if (s >= 0) {
+            if (s != cur) {
+                if (cur >= 0 && (acc_first || acc_dl != 0.0)) {
+                    if (acc_first) atomicAdd(&a.acc[cur].frontier_cells, acc_first);
+                    if (acc_dl != 0.0) atomicAdd(&a.acc[cur].s_front, acc_dl);
+                }
+                cur = s;
+                acc_first = 0;
+                acc_dl = 0.0;
+            }
             const SceneParams &sp = a.sp[s];
             if (i == sp.pt_off) a.fstart[s] = (int)run;
             if (f[k]) {
                 if (run < (uint32_t)a.n_total) a.frontier[run] = i - sp.pt_off;
                 const int old = atomicAdd(&a.hcand[sp.h_off + a.hcell[i]], 1);
-                first = old == 0;
-                dl = nlogn_step(a.nlogn, old);
+                acc_first += old == 0;
+                acc_dl += nlogn_step(a.nlogn, old);
             }
             if (i == a.n_total - 1) a.fstart[a.n_scenes] = (int)(run + f[k]);
         }
         run += f[k];
-        const unsigned m = scene_run_mask(s);
-        const int fc = run_sum_i32(m, first);
-        const double sd = run_sum_f64(m, dl);
-        if (s >= 0 && run_leader(m)) {
-            if (fc) atomicAdd(&a.acc[s].frontier_cells, fc);
-            if (sd != 0.0) atomicAdd(&a.acc[s].s_front, sd);
-        }
+    }
+    const unsigned m = scene_run_mask(cur);
+    const int fc = run_sum_i32(m, acc_first);
+    const double sd = run_sum_f64(m, acc_dl);
+    if (cur >= 0 && run_leader(m)) {
+        if (fc) atomicAdd(&a.acc[cur].frontier_cells, fc);
+        if (sd != 0.0) atomicAdd(&a.acc[cur].s_front, sd);
     }
 }
 
 // ============================================================================ k_select
 
-__device__ void bitonic_sort_1024(uint32_t *v)
+// Truncated order statistic: the rank-r smallest of the sampled values,
+// truncated to its sign, exponent and top 3 mantissa bits.  Truncation is
+// monotone, so that value is exactly the 12-bit bin (bits >> 20) in which the
+// cumulative histogram first exceeds r: a 2048-bin shared histogram and one
+// block scan replace a full sort.  Values are non-negative (or +inf).
+constexpr int kTruncBins = 2048;
+
+__device__ uint32_t trunc_select(const uint32_t *hist, int rank, uint32_t *s_warp, int *s_bin)
 {
-    for (int k = 2; k <= kMedianSample; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int idx = threadIdx.x; idx < kMedianSample; idx += kThreads) {
-                const int ixj = idx ^ j;
-                if (ixj > idx) {
-                    const uint32_t x = v[idx], y = v[ixj];
-                    const bool up = (idx & k) == 0;
-                    if ((x > y) == up) {
-                        v[idx] = y;
-                        v[ixj] = x;
-                    }
-                }
+    constexpr int per = kTruncBins / kThreads;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < per; ++k) sum += hist[threadIdx.x * per + k];
+    uint32_t tot;
+    uint32_t pre = block_exclusive_scan(sum, &tot, s_warp);
+    if (pre <= (uint32_t)rank && (uint32_t)rank < pre + sum) {
+        for (int k = 0; k < per; ++k) {
+            pre += hist[threadIdx.x * per + k];
+            if ((uint32_t)rank < pre) {
+                *s_bin = threadIdx.x * per + k;
+                break;
             }
-            __syncthreads();
         }
     }
+    __syncthreads();
+    const uint32_t bin = (uint32_t)*s_bin;
+    __syncthreads();
+    return bin << 20;
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
 {
-    __shared__ uint32_t s_c[kMedianSample];
-    __shared__ uint32_t s_d[kMedianSample];
+    __shared__ uint32_t s_hc[kTruncBins];
+    __shared__ uint32_t s_hd[kTruncBins];
+    __shared__ uint32_t s_warp[kThreads / 32];
+    __shared__ int s_bin;
     __shared__ float s_feat[8];
     __shared__ float s_h1[64];
     __shared__ float s_h2[64];
@@ -268,25 +291,24 @@ __global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
     const int s = blockIdx.x;
     const SceneParams sp = a.sp[s];
     const int ns = min(sp.n, kMedianSample);
-    for (int k = threadIdx.x; k < kMedianSample; k += kThreads) {
-        uint32_t cb = 0x7f800000u, db = 0x7f800000u;
-        if (k < ns) {
-            const int i = sp.pt_off + k;
-            const float d1 = __fsqrt_rn(a.d1sq[i]);
-            const float d2 = __fsqrt_rn(a.d2sq[i]);
-            cb = __float_as_uint(__fsub_rn(d2, d1));
-            db = __float_as_uint(d2);
-        }
-        s_c[k] = cb;
-        s_d[k] = db;
+    for (int k = threadIdx.x; k < kTruncBins; k += kThreads) {
+        s_hc[k] = 0u;
+        s_hd[k] = 0u;
     }
     __syncthreads();
-    bitonic_sort_1024(s_c);
-    bitonic_sort_1024(s_d);
-    const float med_c = __uint_as_float(s_c[(ns - 1) / 2] & 0xFFF00000u);
-    // reference d2 for the search-grid cell side: a quantile of the sample
+    for (int k = threadIdx.x; k < ns; k += kThreads) {
+        const int i = sp.pt_off + k;
+        const float d1 = __fsqrt_rn(a.d1sq[i]);
+        const float d2 = __fsqrt_rn(a.d2sq[i]);
+        // c >= 0 and d2 >= 0 (or +inf): bit patterns >> 20 lie in [0, 2047]; NaN is clamped
+        atomicAdd(&s_hc[min(__float_as_uint(__fsub_rn(d2, d1)) >> 20, (uint32_t)kTruncBins - 1)], 1u);
+        atomicAdd(&s_hd[min(__float_as_uint(d2) >> 20, (uint32_t)kTruncBins - 1)], 1u);
+    }
+    __syncthreads();
+    // lower median of the clearances; the cell-size reference quantile of d2
+    const float med_c = __uint_as_float(trunc_select(s_hc, (ns - 1) / 2, s_warp, &s_bin));
     const int qi = min(ns - 1, max(0, (int)(a.cell_quantile * (float)(ns - 1))));
-    const float med_d2 = __uint_as_float(s_d[qi] & 0xFFF00000u);
+    const float med_d2 = __uint_as_float(trunc_select(s_hd, qi, s_warp, &s_bin));
 
     int strat = STRAT_INC;
     if (a.mode == MODE_STEP) {
