@@ -85,6 +85,47 @@ __device__ __forceinline__ float sqdist(const float4 a, const float4 b)
     return s;
 }
 
+// Squared distances of two candidates a, b to the query p.  The differences
+// and squares use packed FP32 pairs (Blackwell f32x2 arithmetic, every
+// element rounded to nearest on its own); the two additions stay scalar
+// add.rn.f32, which the code generator never fuses with a multiply.  Each
+// result therefore equals sqdist<DIM>(p, .) bit for bit.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+template <int DIM>
+__device__ __forceinline__ void sqdist_pair(const float4 p, const float4 a, const float4 b, float &Da, float &Db)
+{
+    unsigned long long dx, dy, sx, sy;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(pack2(a.x, b.x)), "l"(pack2(p.x, p.x)));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(pack2(a.y, b.y)), "l"(pack2(p.y, p.y)));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(sx) : "l"(dx));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(sy) : "l"(dy));
+    float xa, xb, ya, yb;
+    unpack2(sx, xa, xb);
+    unpack2(sy, ya, yb);
+    Da = __fadd_rn(xa, ya);
+    Db = __fadd_rn(xb, yb);
+    if (DIM == 3) {
+        unsigned long long dz, sz;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(pack2(a.z, b.z)), "l"(pack2(p.z, p.z)));
+        asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(sz) : "l"(dz));
+        float za, zb;
+        unpack2(sz, za, zb);
+        Da = __fadd_rn(Da, za);
+        Db = __fadd_rn(Db, zb);
+    }
+}
+
 // Cell coordinate of one axis: floor(x * g) clamped to [0, g-1].
 __device__ __forceinline__ int cell_coord(float x, int g, float gf)
 {

@@ -488,8 +488,8 @@ __device__ __forceinline__ void visit_range(const SearchCtx &c, int lo, int hi, 
         const float4 q0 = c.sorted[k];
         const float4 q1 = c.sorted[k + 1];
         const int j0 = __float_as_int(q0.w), j1 = __float_as_int(q1.w);
-        const float D0 = sqdist<DIM>(c.p, q0);
-        const float D1 = sqdist<DIM>(c.p, q1);
+        float D0, D1;
+        sqdist_pair<DIM>(c.p, q0, q1, D0, D1);
         if (D0 <= t.d2 && j0 != c.gi) top3_insert(t, D0, j0);
         if (D1 <= t.d2 && j1 != c.gi) top3_insert(t, D1, j1);
     }
@@ -574,17 +574,12 @@ __device__ __forceinline__ bool grid_search(const SearchCtx &c, Top3 &t, float &
         rng[k * kThreads] = make_int2(lo, hi);
         total += hi - lo;
     }
-    {
-        int k = 0;
-        int2 cur = rng[0];
-        for (int m = 0; m < total; ++m) {
-            while (cur.x >= cur.y) cur = rng[(++k) * kThreads];
-            const float4 q = c.sorted[cur.x++];
-            const int j = __float_as_int(q.w);
-            const float D = sqdist<DIM>(c.p, q);
-            if (D <= t.d2 && j != c.gi) top3_insert(t, D, j);
-        }
+#pragma unroll 1
+    for (int k = 0; k < NR; ++k) {
+        const int2 r = rng[k * kThreads];
+        visit_range<DIM>(c, r.x, r.y, t);
     }
+    (void)total;
 
     const int gm = c.g - 1;
     int x0 = max(cx - 1, 0), x1 = min(cx + 1, gm);
