@@ -279,6 +279,8 @@ def main():
     ap.add_argument("--compare-steps", type=int, default=256)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--allpairs-sizes", default="40000,80000,200000",
+                    help="sizes for the all-pairs timing ('' to skip)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -467,6 +469,32 @@ def main():
     e2e = {"value": N * E / el * (n_all / N), "unit": UNIT, "h2d_bytes_per_step": row_bytes,
            "d2h_bytes_per_step": int(S * cert.SCENE_DTYPE.itemsize), "steps": E}
 
+    # ---- the all-pairs pass (exact brute force) at the paper's Table 2 sizes
+    allpairs = None
+    if args.allpairs_sizes:
+        allpairs = {"peak_fp32_ops_per_s": None, "ops_per_pair": 8 if dim == 3 else 5, "rows": []}
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = nsm * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6
+        allpairs["peak_fp32_ops_per_s"] = peak
+        allpairs["peak_source"] = f"{nsm} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2032.0):.0f} MHz (one FP32 op per lane per cycle)"
+        for nap in [int(x) for x in args.allpairs_sizes.split(",")]:
+            pts = torch.rand((nap, 3), generator=torch.Generator().manual_seed(nap)).cuda()
+            cert.cert_allpairs(pts)
+            torch.cuda.synchronize()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            ea.record(stream)
+            for _ in range(reps):
+                cert.cert_allpairs(pts)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            t_ms = ea.elapsed_time(eb) / reps
+            pairs = nap * (nap - 1)
+            ops = allpairs["ops_per_pair"] * pairs / (t_ms * 1e-3)
+            allpairs["rows"].append({"n": nap, "ms": t_ms, "gpairs_per_s": pairs / (t_ms * 1e-3) / 1e9,
+                                     "fp32_frac": ops / peak})
+            del pts
+
     cb = None
     if rank == 0 and args.cpu_seconds > 0:
         cb, _, _ = cpu_baseline(frames, offsets, dim, budget_s=args.cpu_seconds)
@@ -484,7 +512,7 @@ def main():
                 "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
-                "step_counts": step_counts, "compare": compare, "regret": regret,
+                "step_counts": step_counts, "compare": compare, "regret": regret, "allpairs": allpairs,
                 "status": cert.STATUS_NAMES[rc] if 0 <= rc < len(cert.STATUS_NAMES) else rc}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -5,7 +5,9 @@
 // coordinates are staged into shared memory 2048 points at a time by a TMA bulk
 // copy (cp.async.bulk + mbarrier), every thread keeps the running top-3 of its
 // four queries in registers, and candidates are visited in ascending index so
-// a strict '<' realises the lowest-index tie-break inside a chunk.  Chunks are
+// a strict '<' realises the lowest-index tie-break inside a chunk.  Distances
+// of a candidate to two queries come from one packed FP32 pair operation
+// (f32x2 differences and squares, scalar additions; bit-identical).  Chunks are
 // merged afterwards in chunk order with the full lexicographic key, which
 // gives a deterministic result independent of how the j-range was split.
 // The work is plain FP32 arithmetic (no tensor cores: the inner dimension is
@@ -97,6 +99,14 @@ __global__ void __launch_bounds__(kApThreads) k_allpairs(const APArgs a)
     }
     __syncthreads();
 
+    // queries packed pairwise for the f32x2 arithmetic
+    unsigned long long qx[kApQ / 2], qy[kApQ / 2], qz[kApQ / 2];
+#pragma unroll
+    for (int k = 0; k < kApQ / 2; ++k) {
+        qx[k] = pack2(qp[2 * k].x, qp[2 * k + 1].x);
+        qy[k] = pack2(qp[2 * k].y, qp[2 * k + 1].y);
+        qz[k] = pack2(qp[2 * k].z, qp[2 * k + 1].z);
+    }
     const int j0 = it.chunk * sp.ap_chunk;
     const int j1 = min(sp.n, j0 + sp.ap_chunk);
     uint32_t phase = 0;
@@ -119,9 +129,11 @@ __global__ void __launch_bounds__(kApThreads) k_allpairs(const APArgs a)
             const float4 c = s_tile[jj];
             const int j = jb + jj;
 #pragma unroll
-            for (int k = 0; k < kApQ; ++k) {
-                const float D = sqdist<DIM>(qp[k], c);
-                if (D < t[k].d2 && j != qi[k]) top3_insert(t[k], D, j);
+            for (int k = 0; k < kApQ; k += 2) {
+                float D0, D1;
+                sqdist_qpair<DIM>(qx[k / 2], qy[k / 2], qz[k / 2], c, D0, D1);
+                if (D0 < t[k].d2 && j != qi[k]) top3_insert(t[k], D0, j);
+                if (D1 < t[k + 1].d2 && j != qi[k + 1]) top3_insert(t[k + 1], D1, j);
             }
         }
         __syncthreads();

@@ -126,6 +126,34 @@ __device__ __forceinline__ void sqdist_pair(const float4 p, const float4 a, cons
     }
 }
 
+// Squared distances of one candidate c to two queries whose coordinates are
+// packed pairwise (qx = {x0, x1}, ...): packed differences and squares, scalar
+// additions -- bit-identical to sqdist<DIM>(query, c) for each query.
+template <int DIM>
+__device__ __forceinline__ void sqdist_qpair(unsigned long long qx, unsigned long long qy, unsigned long long qz,
+                                             const float4 c, float &D0, float &D1)
+{
+    unsigned long long dx, dy, sx, sy;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(pack2(c.x, c.x)), "l"(qx));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(pack2(c.y, c.y)), "l"(qy));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(sx) : "l"(dx));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(sy) : "l"(dy));
+    float x0, x1, y0, y1;
+    unpack2(sx, x0, x1);
+    unpack2(sy, y0, y1);
+    D0 = __fadd_rn(x0, y0);
+    D1 = __fadd_rn(x1, y1);
+    if (DIM == 3) {
+        unsigned long long dz, sz;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(pack2(c.z, c.z)), "l"(qz));
+        asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(sz) : "l"(dz));
+        float z0, z1;
+        unpack2(sz, z0, z1);
+        D0 = __fadd_rn(D0, z0);
+        D1 = __fadd_rn(D1, z1);
+    }
+}
+
 // Cell coordinate of one axis: floor(x * g) clamped to [0, g-1].
 __device__ __forceinline__ int cell_coord(float x, int g, float gf)
 {
