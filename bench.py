@@ -220,6 +220,20 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def aggregate(ms, n_points, dist=None, device="cpu"):
+    """Whole-job timing over ranks: the slowest rank's milliseconds and the
+    points all ranks processed (scenes are independent, so nothing else is
+    exchanged)."""
+    if dist is None:
+        return ms, n_points
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    nt = torch.tensor([float(n_points)], dtype=torch.float64, device=device)
+    dist.all_reduce(nt)
+    return float(t.item()), int(nt.item())
+
+
 def graph_loop(ctx, dev_frames, F, eps, strategy, K, use_graph, stream, torch):
     """Time K steps from the start of the ping-pong cycle (state at frame 0);
     the cycle (2F steps, even) is captured once as a CUDA graph and replayed.
@@ -364,15 +378,7 @@ def main():
     clocks = sampler.stop()
     res, rc = ctx.sync(raise_on_status=False)
     assert int(res["n_missed"].sum()) == 0, "safety rule missed a failure"
-    ms_max = ms
-    n_all = N
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        nt = torch.tensor([float(N)], device="cuda")
-        dist.all_reduce(nt)
-        n_all = int(nt.item())
+    ms_max, n_all = aggregate(ms, N, dist, "cuda")
     value = n_all * K / (ms_max / 1e3)
     to_cycle_start()
 

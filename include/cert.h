@@ -263,6 +263,14 @@ cert_status cert_profile_end(cert_ctx *ctx, float *h_ms, int32_t max_steps, int3
 cert_status cert_allpairs_noalloc(const float *d_pos, int64_t n, int32_t dim, const int32_t *d_queries,
                                   int64_t nq, int32_t *d_nn, float *d_d1sq, float *d_d2sq, void *stream);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * thread spins on a flag that nothing sets, the way a chained-scan tile
+ * waits for its predecessor, and gives up after `limit` polls (1 .. 2^24),
+ * latching the timeout bit.  Returns CERT_ETIMEOUT when the wait expired as
+ * designed (the context stays usable), *h_status = latched bits, *h_spins =
+ * polls made.  Synchronises the device; allocates 256 bytes. */
+cert_status cert_selftest_bounded_wait(int32_t limit, uint32_t *h_status, uint32_t *h_spins);
+
 /* Release every resource of the context (synchronises it first). */
 void cert_destroy(cert_ctx *ctx);
 

@@ -69,7 +69,8 @@ EXPORTS = ["cert_init", "cert_step", "cert_step_host", "cert_rebuild", "cert_get
            "cert_version", "cert_profile_begin", "cert_profile_end",
            "cert_allpairs_noalloc", "cert_set_cell_scale", "cert_set_cell_quantile", "cert_get_cell_scale", "cert_autotune",
            "cert_snapshot", "cert_restore", "cert_get_features", "cert_selector_load",
-           "cert_mlp_workspace_bytes", "cert_mlp_forward", "cert_mlp_grad", "cert_mlp_adam"]
+           "cert_mlp_workspace_bytes", "cert_mlp_forward", "cert_mlp_grad", "cert_mlp_adam",
+           "cert_selftest_bounded_wait"]
 MLP_PARAMS = 4866
 N_PHASES = 7
 PHASE_NAMES = ["clear", "prepare", "scan", "select", "scatter_refresh", "search", "finalize"]
@@ -234,6 +235,16 @@ def cert_allpairs_noalloc(pos, queries=None, nn=None, d1sq=None, d2sq=None, stre
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def cert_selftest_bounded_wait(limit=1000):
+    """Run the bounded-wait self-test; returns (status code, latched bits, polls)."""
+    fn = lib().cert_selftest_bounded_wait
+    fn.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    st, sp = ctypes.c_uint32(0), ctypes.c_uint32(0)
+    rc = fn(int(limit), ctypes.byref(st), ctypes.byref(sp))
+    return rc, int(st.value), int(sp.value)
 
 
 def cert_mlp_workspace_bytes(n):

@@ -714,6 +714,48 @@ void cert_destroy(cert_ctx *c)
 
 }  // extern "C"
 
+// ---------------------------------------------------------------- bounded-wait self-test
+
+namespace certk {
+// Spin on a flag nothing ever sets, exactly as the chained scan waits for a
+// predecessor, but with a caller-given iteration limit; on expiry record the
+// timeout in the status word and return.
+__global__ void k_wait_selftest(const uint64_t *flag, uint32_t limit, uint32_t *status, uint32_t *spun)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint32_t spins = 0;
+    while ((ld_acquire_u64(flag) >> 32) == 0u) {
+        if (++spins > limit) {
+            atomicOr(status, ST_TIMEOUT);
+            break;
+        }
+    }
+    *spun = spins;
+}
+}  // namespace certk
+
+extern "C" cert_status cert_selftest_bounded_wait(int32_t limit, uint32_t *h_status, uint32_t *h_spins)
+{
+    if (limit < 1 || limit > (1 << 24)) return fail(nullptr, CERT_EINVAL, "limit must be in [1, 2^24]");
+    char *buf = nullptr;
+    CK((cert_ctx *)nullptr, cudaMalloc((void **)&buf, 256));
+    cudaError_t e = cudaMemset(buf, 0, 256);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>((const uint64_t *)buf, (uint32_t)limit, (uint32_t *)(buf + 64),
+                                   (uint32_t *)(buf + 128));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    uint32_t st = 0, sp = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, buf + 64, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&sp, buf + 128, 4, cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(nullptr, "cert_selftest_bounded_wait", e);
+    if (h_status) *h_status = st;
+    if (h_spins) *h_spins = sp;
+    return (st & ST_TIMEOUT) ? CERT_ETIMEOUT : CERT_OK;
+}
+
 // ---------------------------------------------------------------- cert_allpairs
 
 namespace certk {
