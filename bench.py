@@ -26,6 +26,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -39,7 +40,7 @@ METRIC = "certified point-updates/s"
 UNIT = "point-updates/s"
 KERNELS_PER_STEP = 7   # prepare, scan, select, scatter_refresh, search, far, finalize
 
-# Per-phase algorithmic (compulsory DRAM) bytes, see DESIGN.md "Roofline".
+# Per-phase algorithmic (compulsory DRAM) bytes.
 #   prepare: read p' (4 dim) + p (16), write packed p' (16), (bucket, rank) (8), cell (4),
 #            bucket-count and cell-count atomics (8 + 8)
 #   scan:    read d1^2, d2^2 (8), write frontier flag (1) per point; bucket count read +
@@ -81,10 +82,10 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"cert_bench_clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -286,6 +287,7 @@ def main():
     ap.add_argument("--cell-quantile", type=float, default=0.0, help="d2 quantile of the reference (0: default)")
     ap.add_argument("--bucket-factor", type=int, default=0, help="hashed buckets per scene / next_pow2(n)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--clocks-out", default=None, help="keep the nvidia-smi clock samples here ({rank} expands)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--prof-steps", type=int, default=200)
@@ -366,7 +368,7 @@ def main():
 
     # ---- the timed region: K steps of the chosen strategy
     K = args.steps
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clocks_out.replace("{rank}", str(rank)) if args.clocks_out else None)
     sampler.start()
     time.sleep(0.3)
     if dist:

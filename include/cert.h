@@ -52,7 +52,7 @@ typedef enum {
 
 typedef enum {
     CERT_AUTO = 0,        /* per scene: the loaded selector's choice, else the policy */
-    CERT_INCREMENTAL = 1, /* refresh safe certificates, grid-repair frontier (Alg. 1) */
+    CERT_INCREMENTAL = 1, /* O(1) refresh where provable, grid repair of the rest (Alg. 1) */
     CERT_REBUILD = 2,     /* grid search for every point (O(N) rebuild)               */
     CERT_ALLPAIRS = 3,    /* exact all-pairs pass for every point (O(N^2))            */
     CERT_THRESHOLD = 4    /* per scene: incremental iff |F|/N < 1/ln N, else rebuild

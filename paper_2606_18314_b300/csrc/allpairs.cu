@@ -213,9 +213,10 @@ __global__ void k_allpairs_merge_step(const APArgs a, const APMergeOut o)
         }
         sa.nn[i] = n1;
         sa.nn2[i] = n2;
+        sa.nn3[i] = (t.j2 != 0x7fffffff) ? t.j2 - sp.pt_off : -1;
         sa.d1sq[i] = t.d0;
         sa.d2sq[i] = t.d1;
-        sa.L[i] = sqrt_lower(t.d2);
+        sa.L[i] = sqrt_lower(t.d2);   // every point beyond the top-3 is at least this far
     }
     const unsigned m = scene_run_mask(s);
     const int nsr = run_sum_i32(m, valid ? 1 : 0);

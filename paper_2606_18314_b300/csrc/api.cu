@@ -38,7 +38,7 @@ struct cert_ctx {
     int32_t *fstart = nullptr, *scene_of = nullptr;
     float4 *pos[2] = {nullptr, nullptr};
     int cur = 0;
-    int32_t *nn = nullptr, *nn2 = nullptr;
+    int32_t *nn = nullptr, *nn2 = nullptr, *nn3 = nullptr;
     float *d1sq = nullptr, *d2sq = nullptr, *L = nullptr;
     int32_t *hcell = nullptr, *frontier = nullptr;
     uint8_t *inF = nullptr, *failed = nullptr, *sflag = nullptr;
@@ -157,6 +157,7 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.far_count = c->far_count;
     a.nn = c->nn;
     a.nn2 = c->nn2;
+    a.nn3 = c->nn3;
     a.d1sq = c->d1sq;
     a.d2sq = c->d2sq;
     a.L = c->L;
@@ -293,7 +294,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_res = cv.take<cert_scene_result>(S), o_status = cv.take<uint32_t>(4),
                  o_fstart = cv.take<int32_t>(S + 1), o_scene = cv.take<int32_t>(N),
                  o_pos0 = cv.take<float4>(N), o_pos1 = cv.take<float4>(N), o_nn = cv.take<int32_t>(N),
-                 o_nn2 = cv.take<int32_t>(N), o_d1 = cv.take<float>(N), o_d2 = cv.take<float>(N),
+                 o_nn2 = cv.take<int32_t>(N), o_nn3 = cv.take<int32_t>(N), o_d1 = cv.take<float>(N), o_d2 = cv.take<float>(N),
                  o_L = cv.take<float>(N), o_hcell = cv.take<int32_t>(N), o_front = cv.take<int32_t>(N),
                  o_inF = cv.take<uint8_t>(Npad), o_failed = cv.take<uint8_t>(Npad),
                  o_sflag = cv.take<uint8_t>(Npad), o_brank = cv.take<int2>(N), o_sorted = cv.take<float4>(N),
@@ -327,6 +328,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->pos[1] = (float4 *)(b + o_pos1);
     c->nn = (int32_t *)(b + o_nn);
     c->nn2 = (int32_t *)(b + o_nn2);
+    c->nn3 = (int32_t *)(b + o_nn3);
     c->d1sq = (float *)(b + o_d1);
     c->d2sq = (float *)(b + o_d2);
     c->L = (float *)(b + o_L);
@@ -611,6 +613,7 @@ static std::vector<std::pair<void *, size_t>> snapshot_pieces(cert_ctx *c)
 {
     const size_t N = size_t(c->N), S = size_t(c->S);
     return {{c->pos[c->cur], N * sizeof(float4)},  {c->nn, N * 4},         {c->nn2, N * 4},
+            {c->nn3, N * 4},
             {c->d1sq, N * 4},                      {c->d2sq, N * 4},       {c->L, N * 4},
             {c->st, S * sizeof(SceneState)},      {c->res, S * sizeof(cert_scene_result)},
             {c->hcell, N * 4},                     {c->frontier, N * 4},   {c->fstart, (S + 1) * 4},

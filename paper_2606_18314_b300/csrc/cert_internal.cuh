@@ -14,7 +14,7 @@ namespace certk {
 constexpr int kThreads = 256;
 constexpr int kScanItems = 8;                          // items per thread in a scan tile
 constexpr int kScanTile = kThreads * kScanItems;       // 2048 items per tile
-constexpr int kSearchChunk = kThreads;                 // sorted slots per search CTA
+constexpr int kSearchChunk = 4 * kThreads;             // sorted slots per search CTA
 constexpr int kMedianSample = 1024;                    // points sampled for the medians
 constexpr int kMaxSearchRes = 2048;                    // search-grid cells per axis, cap
 constexpr int kMaxExtend = 16;                         // face extensions before a warp scans the scene
@@ -67,6 +67,12 @@ struct SceneAcc {
 struct Top3 {
     float d0, d1, d2;
     int j0, j1, j2;
+};
+
+// Four smallest keys: the search keeps (nn, nn2, nn3) and bounds the rest by the fourth.
+struct Top4 {
+    float d0, d1, d2, d3;
+    int j0, j1, j2, j3;
 };
 
 // ----------------------------------------------------------------------------- arithmetic
@@ -193,6 +199,14 @@ __device__ __forceinline__ uint32_t row_base(int cy, int cz, int g, bool dense)
     return mix32((DIM == 3) ? ((uint32_t)cz * 0x10001u + (uint32_t)cy) : (uint32_t)cy);
 }
 
+template <typename T>
+__device__ __forceinline__ void swapv(T &a, T &b)
+{
+    const T t = a;
+    a = b;
+    b = t;
+}
+
 __device__ __forceinline__ bool key_less(float da, int ja, float db, int jb)
 {
     return da < db || (da == db && ja < jb);
@@ -225,6 +239,43 @@ __device__ __forceinline__ void top3_insert(Top3 &t, float D, int j)
     } else {
         t.d2 = D;
         t.j2 = j;
+    }
+}
+
+__device__ __forceinline__ void top4_reset(Top4 &t)
+{
+    t.d0 = t.d1 = t.d2 = t.d3 = __int_as_float(0x7f800000);
+    t.j0 = t.j1 = t.j2 = t.j3 = 0x7fffffff;
+}
+
+// Insert (D, j) keeping the four lexicographically smallest distinct keys;
+// an index already held is ignored.
+__device__ __forceinline__ void top4_insert(Top4 &t, float D, int j)
+{
+    if (!key_less(D, j, t.d3, t.j3)) return;
+    if (j == t.j0 || j == t.j1 || j == t.j2) return;
+    if (key_less(D, j, t.d2, t.j2)) {
+        t.d3 = t.d2;
+        t.j3 = t.j2;
+        if (key_less(D, j, t.d1, t.j1)) {
+            t.d2 = t.d1;
+            t.j2 = t.j1;
+            if (key_less(D, j, t.d0, t.j0)) {
+                t.d1 = t.d0;
+                t.j1 = t.j0;
+                t.d0 = D;
+                t.j0 = j;
+            } else {
+                t.d1 = D;
+                t.j1 = j;
+            }
+        } else {
+            t.d2 = D;
+            t.j2 = j;
+        }
+    } else {
+        t.d3 = D;
+        t.j3 = j;
     }
 }
 

@@ -38,8 +38,8 @@ struct StepArgs {
     int32_t *far_list;             // [n] sorted slots left to the far pass
     int32_t *far_count;            // number of entries in far_list (zeroed every call)
     // certificates
-    int32_t *nn, *nn2;
-    float *d1sq, *d2sq, *L;
+    int32_t *nn, *nn2, *nn3;       // nearest, runner-up, third stored candidate (-1: none)
+    float *d1sq, *d2sq, *L;        // L: lower bound on the distance to every other point
     // step outputs
     int32_t *hcell, *hocc, *hfail, *hcand;
     uint8_t *inF, *failed;

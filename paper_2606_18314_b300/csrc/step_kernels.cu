@@ -13,7 +13,8 @@
 //   k_select           per scene: truncated medians, next search resolution,
 //                      the strategy (forced, policy or learned selector)
 //   k_scatter_refresh  counting-sort scatter into cell order; O(1) refresh of
-//                      safe certificates from the extended certificate
+//                      every certificate that its extended certificate still
+//                      proves (frontier points included)
 //   k_search           grid repair of the flagged points: top-2 over the 3^d
 //                      block, widened until the runner-up is enclosed (Alg. 1
 //                      block loop; Cor. A.2 widening)
@@ -23,10 +24,13 @@
 // paper leaves d1, d2 of safe points stale while every certificate here is
 // exact each step): besides (nn, d1^2, d2^2) each point keeps its runner-up
 // index nn2 and a lower bound L on the distance to every point other than nn
-// and nn2.  A step moves any pair apart or together by at most 2 eps_t
-// (triangle inequality, as in Lemma 1), so L - 2 eps_t bounds the next step;
-// when both fresh distances to nn and nn2 stay below it the top-2 is exactly
-// {nn, nn2} in fresh order, otherwise the point is repaired by a search.
+// and nn2.  A step changes the distance from i to any j by at most
+// |p'_i - p_i| + eps_t (triangle inequality, as in Lemma 1), so L minus that
+// bounds the next step; when both fresh distances to nn and nn2 stay below it
+// the top-2 is exactly {nn, nn2} in fresh order, otherwise the point is
+// repaired by a search.  The test is independent of the safety rule, so a
+// frontier point it proves is repaired in O(1) too (a change of nn is then
+// found by the reordering of {nn, nn2}).
 #include "cert_internal.cuh"
 #include "cert_launch.h"
 
@@ -55,11 +59,13 @@ __global__ void __launch_bounds__(kThreads) k_prepare(const StepArgs a)
             p.z = (DIM == 3) ? q[2] : 0.0f;
             p.w = 0.0f;
             if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) atomicOr(a.status, ST_NONFINITE);
-            a.pos_new[i] = p;
             if (a.mode == MODE_STEP) {
+                // squared displacement of this point; kept in w for the refresh
                 const float D = sqdist<DIM>(a.pos_old[i], p);
                 dbits = (D >= 0.0f) ? __float_as_uint(D) : 0u;
+                p.w = D;
             }
+            a.pos_new[i] = p;
         }
         // hashed search grid: bucket of the cell, rank inside the bucket
         const int g = a.st[s].g_cur;
@@ -407,7 +413,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
 {
     const int i = blockIdx.x * kThreads + threadIdx.x;
     const bool valid = i < a.n_total;
-    int s = -1, changed = 0, first = 0;
+    int s = -1, changed = 0, missed = 0, first = 0;
     double dl = 0.0;
     if (valid) {
         s = a.scene_of[i];
@@ -421,25 +427,48 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
         const float4 p = a.pos_new[i];
         a.sorted[slot] = make_float4(p.x, p.y, p.z, __int_as_float(i));
         bool need = true;
-        if (a.mode == MODE_STEP && a.st[s].strategy == STRAT_INC && !a.inF[i]) {
-            const int na = a.nn[i], nb = a.nn2[i];
+        if (a.mode == MODE_STEP && a.st[s].strategy == STRAT_INC) {
+            const int na = a.nn[i], nb = a.nn2[i], nc = a.nn3[i];
             if ((unsigned)na < (unsigned)sp.n && (unsigned)nb < (unsigned)sp.n) {
-                const float Da = sqdist<DIM>(p, a.pos_new[sp.pt_off + na]);
-                const float Db = sqdist<DIM>(p, a.pos_new[sp.pt_off + nb]);
-                const float two_eps_up = __fmul_ru(eps_of(a.acc, s), 2.0f + 0x1p-18f);
-                const float Lnew = __fsub_rd(a.L[i], two_eps_up);
-                if (Lnew > 0.0f && __fmul_ru(fmaxf(Da, Db), 1.0f + 0x1p-19f) < __fmul_rd(Lnew, Lnew)) {
+                // fresh keys of the three stored candidates, sorted
+                float d1 = sqdist<DIM>(p, a.pos_new[sp.pt_off + na]);
+                float d2 = sqdist<DIM>(p, a.pos_new[sp.pt_off + nb]);
+                float d3 = __int_as_float(0x7f800000);
+                int j1 = na, j2 = nb, j3 = 0x7fffffff;
+                if ((unsigned)nc < (unsigned)sp.n) {
+                    d3 = sqdist<DIM>(p, a.pos_new[sp.pt_off + nc]);
+                    j3 = nc;
+                }
+                if (key_less(d2, j2, d1, j1)) {
+                    swapv(d1, d2);
+                    swapv(j1, j2);
+                }
+                if (key_less(d3, j3, d2, j2)) {
+                    swapv(d2, d3);
+                    swapv(j2, j3);
+                    if (key_less(d2, j2, d1, j1)) {
+                        swapv(d1, d2);
+                        swapv(j1, j2);
+                    }
+                }
+                // any distance from i changed by at most |p'_i - p_i| + eps_t
+                // (triangle inequality); both terms rounded up with slack
+                const float shrink = __fmul_ru(__fadd_ru(__fsqrt_ru(p.w), eps_of(a.acc, s)), 1.0f + 0x1p-18f);
+                const float Lnew = __fsub_rd(a.L[i], shrink);
+                // every point outside {nn, nn2, nn3} is now at least Lnew away, so
+                // when the second key is closer the top-2 is the first two keys
+                if (Lnew > 0.0f && __fmul_ru(d2, 1.0f + 0x1p-19f) < __fmul_rd(Lnew, Lnew)) {
                     need = false;
-                    const bool sw = key_less(Db, nb, Da, na);
-                    const int n1 = sw ? nb : na, n2 = sw ? na : nb;
-                    a.nn[i] = n1;
-                    a.nn2[i] = n2;
-                    a.d1sq[i] = sw ? Db : Da;
-                    a.d2sq[i] = sw ? Da : Db;
+                    a.nn[i] = j1;
+                    a.nn2[i] = j2;
+                    a.nn3[i] = (j3 != 0x7fffffff) ? j3 : -1;
+                    a.d1sq[i] = d1;
+                    a.d2sq[i] = d2;
                     a.L[i] = Lnew;
-                    changed = n1 != na;
+                    changed = j1 != na;
                     a.failed[i] = (uint8_t)changed;
                     if (changed) {
+                        missed = !a.inF[i];
                         const int old = atomicAdd(&a.hfail[sp.h_off + a.hcell[i]], 1);
                         first = old == 0;
                         dl = nlogn_step(a.nlogn, old);
@@ -452,12 +481,12 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
     if (a.mode != MODE_STEP) return;  // uniform across the grid
     const unsigned m = scene_run_mask(s);
     const int nc = run_sum_i32(m, changed);
+    const int nm = run_sum_i32(m, missed);
     const int fc = run_sum_i32(m, first);
     const double sd = run_sum_f64(m, dl);
     if (s >= 0 && run_leader(m) && nc) {
-        // refreshed points are never in F, so each change here is also a miss
         atomicAdd(&a.acc[s].n_failed, nc);
-        atomicAdd(&a.acc[s].n_missed, nc);
+        atomicAdd(&a.acc[s].n_missed, nm);
         atomicAdd(&a.acc[s].failed_cells, fc);
         atomicAdd(&a.acc[s].s_fail, sd);
     }
@@ -477,27 +506,31 @@ struct SearchCtx {
     bool dense;
 };
 
-// Visit the sorted slots [lo, hi), two candidate loads in flight.
+// Visit the sorted slots [lo, hi) two candidates at a time; the next pair's
+// loads are issued before the current pair's distances.
 template <int DIM>
-__device__ __forceinline__ void visit_range(const SearchCtx &c, int lo, int hi, Top3 &t)
+__device__ __forceinline__ void visit_range(const SearchCtx &c, int lo, int hi, Top4 &t)
 {
     lo = max(lo, c.pt_off);          // a bucket range never leaves its scene
     hi = min(hi, c.pt_off + c.n);
+    if (lo >= hi) return;
+    float4 n0 = c.sorted[lo];
+    float4 n1 = (lo + 1 < hi) ? c.sorted[lo + 1] : n0;
     int k = lo;
     for (; k + 1 < hi; k += 2) {
-        const float4 q0 = c.sorted[k];
-        const float4 q1 = c.sorted[k + 1];
+        const float4 q0 = n0, q1 = n1;
+        if (k + 2 < hi) n0 = c.sorted[k + 2];
+        if (k + 3 < hi) n1 = c.sorted[k + 3];
         const int j0 = __float_as_int(q0.w), j1 = __float_as_int(q1.w);
         float D0, D1;
         sqdist_pair<DIM>(c.p, q0, q1, D0, D1);
-        if (D0 <= t.d2 && j0 != c.gi) top3_insert(t, D0, j0);
-        if (D1 <= t.d2 && j1 != c.gi) top3_insert(t, D1, j1);
+        if (D0 <= t.d3 && j0 != c.gi) top4_insert(t, D0, j0);
+        if (D1 <= t.d3 && j1 != c.gi) top4_insert(t, D1, j1);
     }
-    if (k < hi) {
-        const float4 q = c.sorted[k];
-        const int j = __float_as_int(q.w);
-        const float D = sqdist<DIM>(c.p, q);
-        if (D <= t.d2 && j != c.gi) top3_insert(t, D, j);
+    if (k < hi) {   // odd length: n0 holds slot hi - 1
+        const int j = __float_as_int(n0.w);
+        const float D = sqdist<DIM>(c.p, n0);
+        if (D <= t.d3 && j != c.gi) top4_insert(t, D, j);
     }
 }
 
@@ -530,7 +563,7 @@ __device__ __forceinline__ void row_ranges(const SearchCtx &c, int yr, int zr, i
 }
 
 template <int DIM>
-__device__ __forceinline__ void visit_row(const SearchCtx &c, int yr, int zr, int xl, int xh, Top3 &t)
+__device__ __forceinline__ void visit_row(const SearchCtx &c, int yr, int zr, int xl, int xh, Top4 &t)
 {
     int lo, hi, lo2, hi2;
     row_ranges<DIM>(c, yr, zr, xl, xh, lo, hi, lo2, hi2);
@@ -549,13 +582,13 @@ constexpr float kFaceSlack = 0x1p-17f;   // >> FP error of cell assignment and f
 // Returns false after kMaxExtend layers; such a query is appended to the far
 // list and finished by k_far.
 template <int DIM>
-__device__ __forceinline__ bool grid_search(const SearchCtx &c, Top3 &t, float &Lout, int2 *rng)
+__device__ __forceinline__ bool grid_search(const SearchCtx &c, Top4 &t, float &Lout, int2 *rng)
 {
     const float gf = (float)c.g;
     const int cx = cell_coord(c.p.x, c.g, gf);
     const int cy = cell_coord(c.p.y, c.g, gf);
     const int cz = (DIM == 3) ? cell_coord(c.p.z, c.g, gf) : 0;
-    top3_reset(t);
+    top4_reset(t);
     // The 3^d block.  Fetch every row's slot range first (independent loads),
     // keep them in this thread's column of the shared range table, then walk
     // all rows as one stream so that a warp runs max(sum of lengths) rather
@@ -604,13 +637,13 @@ __device__ __forceinline__ bool grid_search(const SearchCtx &c, Top3 &t, float &
                 side = k;
             }
         if (isinf(f0)) {  // the box covers the whole grid: everything was visited
-            Lout = sqrt_lower(t.d2);
+            Lout = sqrt_lower(t.d3);
             return true;
         }
         const float fs = __fsub_rd(f0, kFaceSlack);
         if (t.j1 != 0x7fffffff && fs > 0.0f &&
             __fmul_ru(t.d1, 1.0f + 0x1p-19f) < __fmul_rd(fs, fs)) {  // runner-up provably enclosed
-            Lout = fminf(sqrt_lower(t.d2), fs);
+            Lout = fminf(sqrt_lower(t.d3), fs);
             return true;
         }
         if (ext >= kMaxExtend) return false;
@@ -638,18 +671,19 @@ __device__ __forceinline__ bool grid_search(const SearchCtx &c, Top3 &t, float &
     }
 }
 
-// Merge the warp's per-lane top-3 lists (butterfly; every lane ends with the result).
-__device__ __forceinline__ void warp_merge_top3(Top3 &t)
+// Merge the warp's per-lane top-4 lists (butterfly; every lane ends with the result).
+__device__ __forceinline__ void warp_merge_top4(Top4 &t)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float e0 = __shfl_xor_sync(kFull, t.d0, o), e1 = __shfl_xor_sync(kFull, t.d1, o),
-                    e2 = __shfl_xor_sync(kFull, t.d2, o);
+                    e2 = __shfl_xor_sync(kFull, t.d2, o), e3 = __shfl_xor_sync(kFull, t.d3, o);
         const int k0 = __shfl_xor_sync(kFull, t.j0, o), k1 = __shfl_xor_sync(kFull, t.j1, o),
-                  k2 = __shfl_xor_sync(kFull, t.j2, o);
-        if (k0 != 0x7fffffff) top3_insert(t, e0, k0);
-        if (k1 != 0x7fffffff) top3_insert(t, e1, k1);
-        if (k2 != 0x7fffffff) top3_insert(t, e2, k2);
+                  k2 = __shfl_xor_sync(kFull, t.j2, o), k3 = __shfl_xor_sync(kFull, t.j3, o);
+        if (k0 != 0x7fffffff) top4_insert(t, e0, k0);
+        if (k1 != 0x7fffffff) top4_insert(t, e1, k1);
+        if (k2 != 0x7fffffff) top4_insert(t, e2, k2);
+        if (k3 != 0x7fffffff) top4_insert(t, e3, k3);
     }
 }
 
@@ -660,7 +694,7 @@ struct SearchOut {
 };
 
 __device__ __forceinline__ SearchOut write_certificate(const StepArgs &a, const SceneParams &sp, int gi,
-                                                       const Top3 &t, float L)
+                                                       const Top4 &t, float L)
 {
     SearchOut o = {0, 0, 0, 0.0};
     const int n1 = (t.j0 != 0x7fffffff) ? t.j0 - sp.pt_off : -1;
@@ -677,78 +711,89 @@ __device__ __forceinline__ SearchOut write_certificate(const StepArgs &a, const 
     }
     a.nn[gi] = n1;
     a.nn2[gi] = n2;
+    a.nn3[gi] = (t.j2 != 0x7fffffff) ? t.j2 - sp.pt_off : -1;
     a.d1sq[gi] = t.d0;
     a.d2sq[gi] = t.d1;
     a.L[gi] = L;
     return o;
 }
 
+// One CTA compacts the flagged slots of kSearchChunk consecutive sorted slots
+// (ascending, so a warp's queries are neighbours and share most rows), then
+// searches them kThreads at a time.
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_search(const StepArgs a)
 {
     constexpr int NR = (DIM == 3) ? 9 : 3;
+    constexpr int PER = kSearchChunk / kThreads;   // slots per thread in the compaction
+    static_assert(PER == 4, "the flag load below reads four flags at once");
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ int s_list[kSearchChunk];
-    __shared__ int2 s_rng[NR * kThreads];      // per-thread row ranges, column-major
-    const int my = blockIdx.x * kSearchChunk + threadIdx.x;
-    const uint32_t f = (my < a.n_total) ? (uint32_t)a.sflag[my] : 0u;
+    __shared__ int2 s_rng[NR * kThreads];          // per-thread row ranges, column-major
+    const int base = blockIdx.x * kSearchChunk + threadIdx.x * PER;
+    // flags beyond n_total are zero up to the padded length (a multiple of the chunk)
+    const uint32_t fw = (base < a.n_total) ? *reinterpret_cast<const uint32_t *>(a.sflag + base) : 0u;
     uint32_t count;
-    const uint32_t pre = block_exclusive_scan(f, &count, s_warp);
-    if (f) s_list[pre] = my;
+    uint32_t pre = block_exclusive_scan(__popc(fw), &count, s_warp);
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+        if ((fw >> (8 * u)) & 0xffu) s_list[pre++] = base + u;
     __syncthreads();
-    if ((int)(threadIdx.x & ~31u) >= (int)count) return;  // whole idle warps leave together
 
-    const bool active = threadIdx.x < count;
-    const int lane = threadIdx.x & 31;
-    int s = -1, gi = -1;
-    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-    SearchOut o = {0, 0, 0, 0.0};
-    if (active) {
-        const int slot = s_list[threadIdx.x];
-        q = a.sorted[slot];
-        gi = __float_as_int(q.w);
-        if ((unsigned)gi >= (unsigned)a.n_total) {  // only after a timed-out scan
-            atomicOr(a.status, ST_TIMEOUT);
-            gi = slot;
+    for (int r0 = 0; r0 < (int)count; r0 += kThreads) {
+        if (r0 + (int)(threadIdx.x & ~31u) >= (int)count) break;  // whole idle warps leave together
+        const int e = r0 + (int)threadIdx.x;
+        const bool active = e < (int)count;
+        int s = -1;
+        SearchOut o = {0, 0, 0, 0.0};
+        if (active) {
+            const int slot = s_list[e];
+            const float4 q = a.sorted[slot];
+            int gi = __float_as_int(q.w);
+            if ((unsigned)gi >= (unsigned)a.n_total) {  // only after a timed-out scan
+                atomicOr(a.status, ST_TIMEOUT);
+                gi = slot;
+            }
+            s = a.scene_of[gi];
+            const SceneParams sp = a.sp[s];
+            const SceneState &st = a.st[s];
+            SearchCtx c;
+            c.sorted = a.sorted;
+            c.bstart = a.bucket_start;
+            c.p = q;
+            c.gi = gi;
+            c.pt_off = sp.pt_off;
+            c.n = sp.n;
+            c.boff = sp.bucket_off;
+            c.T = sp.bucket_mask + 1;
+            c.mask = (uint32_t)sp.bucket_mask;
+            c.g = st.g_cur;
+            c.inv_g = st.inv_g;
+            c.dense = grid_is_dense<DIM>(c.g, c.T);
+            Top4 t;
+            float L;
+            if (grid_search<DIM>(c, t, L, s_rng + threadIdx.x))
+                o = write_certificate(a, sp, gi, t, L);
+            else
+                a.far_list[atomicAdd(a.far_count, 1)] = slot;   // finished by k_far
         }
-        s = a.scene_of[gi];
-        const SceneParams sp = a.sp[s];
-        const SceneState &st = a.st[s];
-        SearchCtx c;
-        c.sorted = a.sorted;
-        c.bstart = a.bucket_start;
-        c.p = q;
-        c.gi = gi;
-        c.pt_off = sp.pt_off;
-        c.n = sp.n;
-        c.boff = sp.bucket_off;
-        c.T = sp.bucket_mask + 1;
-        c.mask = (uint32_t)sp.bucket_mask;
-        c.g = st.g_cur;
-        c.inv_g = st.inv_g;
-        c.dense = grid_is_dense<DIM>(c.g, c.T);
-        Top3 t;
-        float L;
-        if (grid_search<DIM>(c, t, L, s_rng + threadIdx.x))
-            o = write_certificate(a, sp, gi, t, L);
-        else
-            a.far_list[atomicAdd(a.far_count, 1)] = slot;   // finished by k_far
-    }
-    if (a.mode != MODE_STEP) return;
-    // slots of one scene are contiguous, so lanes form contiguous scene runs
-    const unsigned m = scene_run_mask(s);
-    const int nsr = run_sum_i32(m, active ? 1 : 0);
-    const int nc = run_sum_i32(m, o.changed);
-    const int nm = run_sum_i32(m, o.missed);
-    const int fc = run_sum_i32(m, o.first);
-    const double sd = run_sum_f64(m, o.dl);
-    if (s >= 0 && run_leader(m)) {
-        atomicAdd(&a.acc[s].n_searched, nsr);
-        if (nc) {
-            atomicAdd(&a.acc[s].n_failed, nc);
-            atomicAdd(&a.acc[s].n_missed, nm);
-            atomicAdd(&a.acc[s].failed_cells, fc);
-            atomicAdd(&a.acc[s].s_fail, sd);
+        if (a.mode == MODE_STEP) {
+            // slots of one scene are contiguous, so lanes form contiguous scene runs
+            const unsigned m = scene_run_mask(s);
+            const int nsr = run_sum_i32(m, active ? 1 : 0);
+            const int nc = run_sum_i32(m, o.changed);
+            const int nm = run_sum_i32(m, o.missed);
+            const int fc = run_sum_i32(m, o.first);
+            const double sd = run_sum_f64(m, o.dl);
+            if (s >= 0 && run_leader(m)) {
+                atomicAdd(&a.acc[s].n_searched, nsr);
+                if (nc) {
+                    atomicAdd(&a.acc[s].n_failed, nc);
+                    atomicAdd(&a.acc[s].n_missed, nm);
+                    atomicAdd(&a.acc[s].failed_cells, fc);
+                    atomicAdd(&a.acc[s].s_fail, sd);
+                }
+            }
         }
     }
 }
@@ -764,8 +809,8 @@ constexpr int kFarCtas = 2 * 148;
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_far(const StepArgs a)
 {
-    __shared__ float s_d[kThreads / 32][3];
-    __shared__ int s_j[kThreads / 32][3];
+    __shared__ float s_d[kThreads / 32][4];
+    __shared__ int s_j[kThreads / 32][4];
     const int nfar = *a.far_count;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int item = blockIdx.x; item < nfar; item += gridDim.x) {
@@ -775,8 +820,8 @@ __global__ void __launch_bounds__(kThreads) k_far(const StepArgs a)
         if ((unsigned)gi >= (unsigned)a.n_total) gi = slot;
         const int s = a.scene_of[gi];
         const SceneParams sp = a.sp[s];
-        Top3 t;
-        top3_reset(t);
+        Top4 t;
+        top4_reset(t);
         const int end = sp.pt_off + sp.n;
         int j = sp.pt_off + threadIdx.x;
         for (; j + 3 * kThreads < end; j += 4 * kThreads) {
@@ -787,28 +832,28 @@ __global__ void __launch_bounds__(kThreads) k_far(const StepArgs a)
             for (int u = 0; u < 4; ++u) {
                 const int jj = __float_as_int(c[u].w);
                 const float D = sqdist<DIM>(q, c[u]);
-                if (D <= t.d2 && jj != gi) top3_insert(t, D, jj);
+                if (D <= t.d3 && jj != gi) top4_insert(t, D, jj);
             }
         }
         for (; j < end; j += kThreads) {
             const float4 c = a.sorted[j];
             const int jj = __float_as_int(c.w);
             const float D = sqdist<DIM>(q, c);
-            if (D <= t.d2 && jj != gi) top3_insert(t, D, jj);
+            if (D <= t.d3 && jj != gi) top4_insert(t, D, jj);
         }
-        warp_merge_top3(t);
+        warp_merge_top4(t);
         if (lane == 0) {
-            s_d[warp][0] = t.d0; s_d[warp][1] = t.d1; s_d[warp][2] = t.d2;
-            s_j[warp][0] = t.j0; s_j[warp][1] = t.j1; s_j[warp][2] = t.j2;
+            s_d[warp][0] = t.d0; s_d[warp][1] = t.d1; s_d[warp][2] = t.d2; s_d[warp][3] = t.d3;
+            s_j[warp][0] = t.j0; s_j[warp][1] = t.j1; s_j[warp][2] = t.j2; s_j[warp][3] = t.j3;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            Top3 r;
-            top3_reset(r);
+            Top4 r;
+            top4_reset(r);
             for (int w = 0; w < kThreads / 32; ++w)
-                for (int k = 0; k < 3; ++k)
-                    if (s_j[w][k] != 0x7fffffff) top3_insert(r, s_d[w][k], s_j[w][k]);
-            const SearchOut o = write_certificate(a, sp, gi, r, sqrt_lower(r.d2));
+                for (int k = 0; k < 4; ++k)
+                    if (s_j[w][k] != 0x7fffffff) top4_insert(r, s_d[w][k], s_j[w][k]);
+            const SearchOut o = write_certificate(a, sp, gi, r, sqrt_lower(r.d3));
             if (a.mode == MODE_STEP && o.changed) {
                 atomicAdd(&a.acc[s].n_failed, 1);
                 atomicAdd(&a.acc[s].n_missed, o.missed);
