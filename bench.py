@@ -46,15 +46,18 @@ KERNELS_PER_STEP = 7   # prepare, scan, select, scatter_refresh, search, far, fi
 #   scan:    read d1^2, d2^2 (8), write frontier flag (1) per point; bucket count read +
 #            start write (8) per bucket; frontier index (4) per frontier point
 #   scatter_refresh: read (bucket, rank) 8 + bucket start 4 + p' 16, write sorted 16 + flag 1;
-#            refreshed points: read flag 1 + nn, nn2 8 + L 4 + two neighbour positions 32,
-#            write nn, nn2, d1^2, d2^2, L 20 + failed 1
-#   search:  read flag (1) per point; per searched point read query 16 + old nn 4 + flag 1 +
-#            cell 4, write certificate 20 + failed 1
+#            points of incrementally repaired scenes also read nn, nn2, nn3 12 + L 4 + inF 1 +
+#            three neighbour positions 48; the refreshed ones write nn, nn2, nn3, d1^2, d2^2, L 24 +
+#            failed 1
+#   search:  read flag (1) per point; per searched point read query 16 + old nn 4 + inF 1 +
+#            cell 4, write certificate 24 + failed 1
 PHASES = ["clear", "prepare", "scan", "select", "scatter_refresh", "search", "finalize"]
 
 
-def phase_bytes(ph, N, dim, n_buckets, n_front, n_searched, zero_bytes):
-    refreshed = N - n_searched
+def phase_bytes(ph, N, dim, n_buckets, n_front, n_searched, zero_bytes, n_tried=None):
+    """n_tried: points of scenes repaired incrementally (they try the O(1) refresh)."""
+    n_tried = N if n_tried is None else n_tried
+    refreshed = max(0, n_tried - (n_searched - (N - n_tried)))
     if ph == "clear":
         return zero_bytes
     if ph == "prepare":
@@ -62,10 +65,16 @@ def phase_bytes(ph, N, dim, n_buckets, n_front, n_searched, zero_bytes):
     if ph == "scan":
         return N * 9 + n_buckets * 8 + n_front * 4
     if ph == "scatter_refresh":
-        return N * (8 + 4 + 16 + 16 + 1) + refreshed * (1 + 8 + 4 + 32 + 20 + 1)
+        return N * (8 + 4 + 16 + 16 + 1) + n_tried * (12 + 4 + 1 + 48) + refreshed * (24 + 1)
     if ph == "search":
-        return N * 1 + n_searched * (16 + 4 + 1 + 4 + 20 + 1)
+        return N * 1 + n_searched * (16 + 4 + 1 + 4 + 24 + 1)
     return 0
+
+
+# DRAM bytes (read + write) per k_search launch from the ncu capture of the batched
+# 512-scene incremental step (profiles/k_search_batched_512_incremental.md); valid for
+# that workload and kernel version only.
+SEARCH_TRAFFIC_BATCHED = 138.17e6
 
 
 def load_peaks():
@@ -440,7 +449,8 @@ def main():
     for k in range(P):
         do_step()
         r, _ = ctx.sync(raise_on_status=False)
-        counts.append((int(r["n_frontier"].sum()), int(r["n_searched"].sum()), int(r["n_failed"].sum())))
+        tried = int(np.diff(offsets)[np.asarray(r["strategy"]) == cert.CERT_INCREMENTAL].sum())
+        counts.append((int(r["n_frontier"].sum()), int(r["n_searched"].sum()), int(r["n_failed"].sum()), tried))
     prof = ctx.profile_end()
     mean_ms = prof.mean(axis=0)
     peaks, peak_kind = load_peaks()
@@ -448,7 +458,7 @@ def main():
         max(1, args.bucket_factor)
     per_phase = {}
     for j, ph in enumerate(PHASES):
-        byts = [phase_bytes(ph, N, dim, n_buckets, c[0], c[1], 0) for c in counts]
+        byts = [phase_bytes(ph, N, dim, n_buckets, c[0], c[1], 0, c[3]) for c in counts]
         gbs = [b / (t * 1e-3) / 1e9 for b, t in zip(byts, prof[:, j]) if t > 0]
         per_phase[ph] = {"ms": float(mean_ms[j]), "share": float(mean_ms[j] / mean_ms.sum()),
                          "bytes": float(np.mean(byts)), "gbs": float(np.mean(gbs)) if gbs else 0.0}
@@ -457,9 +467,14 @@ def main():
     cnt = np.array(counts, dtype=np.float64)
     step_counts = {"frontier_frac": float(cnt[:, 0].mean() / N), "searched_frac": float(cnt[:, 1].mean() / N),
                    "failed_frac": float(cnt[:, 2].mean() / N)}
+    traffic, traffic_src = None, None
+    if dom == "search" and args.workload == "batched" and args.family is None and args.scenes == 512 and \
+            strat in (cert.CERT_AUTO, cert.CERT_INCREMENTAL):
+        traffic = SEARCH_TRAFFIC_BATCHED
+        traffic_src = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_search launch, same workload"
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
-                "phases": per_phase}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_src,
+                "peak_source": peak_kind, "phases": per_phase}
 
     # ---- end to end through the public API with host buffers (pinned), per step H2D + D2H
     to_cycle_start()

@@ -71,3 +71,47 @@ def test_scale_262144_clusters(torch):
             assert abs(float(res[0]["H"]) - H) <= 1e-6
             assert int(res[0]["failed_cells"]) == mcells and int(res[0]["occupied_cells"]) == C
         prev_nn = ann.cpu().numpy()
+
+
+def test_batched_512_scenes_graph_replay_sampled(torch):
+    """The benchmark's own workload and launch configuration: 512 scenes
+    (2,392,732 points), learned selector, steps replayed from a CUDA graph.
+    Sixteen seeded scenes are checked against the oracle after the replay
+    (certificates bit-exact, failure marks, H within 1e-6); no scene misses a
+    failure."""
+    import bench
+    from paper_2606_18314_b300 import cert, selector
+    frames, off, eps, _ = bench.make_workload("batched", 0, 3)
+    dev = torch.from_numpy(frames).cuda()
+    ctx = cert.Context(dev[0], offsets=off)
+    params, norm = selector.load()
+    ctx.load_selector(params, norm)
+    ctx.set_cell_scale(3.0)
+    ctx.step(dev[1], eps, "auto")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ctx.step(dev[2], eps, "auto")
+        ctx.step(dev[3], eps, "auto")
+    torch.cuda.synchronize()
+    # the capture recorded the two steps without running them; the state is still after frame 1
+    g.replay()
+    torch.cuda.synchronize()
+    res, _ = ctx.sync()
+    assert int(res["n_missed"].sum()) == 0
+    v = ctx.views()
+    nn, d1, d2 = v["nn"].cpu().numpy(), v["d1sq"].cpu().numpy(), v["d2sq"].cpu().numpy()
+    failed = v["failed"].cpu().numpy().astype(bool)
+    rng = np.random.default_rng(512)
+    for s in sorted(rng.choice(len(off) - 1, 16, replace=False)):
+        lo, hi = int(off[s]), int(off[s + 1])
+        prev = oracle.top2(frames[2][lo:hi])
+        cur = oracle.top2(frames[3][lo:hi])
+        assert np.array_equal(nn[lo:hi], cur.nn), s
+        assert np.array_equal(d1[lo:hi].view(np.uint32), cur.d1sq.view(np.uint32)), s
+        assert np.array_equal(d2[lo:hi].view(np.uint32), cur.d2sq.view(np.uint32)), s
+        want_failed = cur.nn != prev.nn
+        assert np.array_equal(failed[lo:hi], want_failed), s
+        g_h = oracle.grid_res(hi - lo, 3)
+        H, mcells, C = oracle.entropy(oracle.cells(frames[3][lo:hi], g_h), want_failed, g_h ** 3)
+        assert abs(float(res["H"][s]) - H) <= 1e-6, s
+        assert int(res["n_failed"][s]) == int(want_failed.sum()), s
