@@ -43,7 +43,8 @@ struct cert_ctx {
     int32_t *hcell = nullptr, *frontier = nullptr;
     uint8_t *inF = nullptr, *failed = nullptr, *sflag = nullptr;
     int2 *brank = nullptr;
-    float4 *sorted = nullptr;
+    float4 *squad = nullptr;
+    int64_t n_quads = 0;
     int32_t *bucket_start = nullptr;
     int32_t *far_list = nullptr, *far_count = nullptr;
     double *nlogn = nullptr;
@@ -151,7 +152,7 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.bucket_count = c->bucket_count;
     a.bucket_start = c->bucket_start;
     a.brank = c->brank;
-    a.sorted = c->sorted;
+    a.squad = c->squad;
     a.sflag = c->sflag;
     a.far_list = c->far_list;
     a.far_count = c->far_count;
@@ -252,7 +253,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
 
     // ---- per-scene layout
     c->h_sp.resize(c->S);
-    int64_t boff = 0, hoff = 0, apoff = 0, total_qb = 0;
+    int64_t boff = 0, hoff = 0, apoff = 0, total_qb = 0, quads = 0;
     for (int k = 0; k < c->S; ++k) total_qb += ceil_div(off[k + 1] - off[k], kApQBlock);
     const int64_t nch_all = std::min<int64_t>(64, std::max<int64_t>(1, ceil_div(148 * 8, total_qb)));
     std::vector<APItem> items;
@@ -262,6 +263,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
         const int64_t n = off[k + 1] - off[k];
         p.pt_off = (int32_t)off[k];
         p.n = (int32_t)n;
+        p.s_off = (int32_t)(4 * quads);
+        quads += ceil_div(n, 4);
         const int T = next_pow2(std::max<int64_t>(n, 16)) * c->bucket_factor;
         p.bucket_off = (int32_t)boff;
         p.bucket_mask = T - 1;
@@ -279,6 +282,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
         for (int ch = 0; ch < nch; ++ch)
             for (int qb = 0; qb < nqb; ++qb) items.push_back({k, qb, ch, 0});
     }
+    c->n_quads = quads;
     c->n_buckets = (int)boff;
     c->n_buckets_pad = (int)ceil_div(boff + 1, kScanTile) * kScanTile;
     c->ntiles_b = c->n_buckets_pad / kScanTile;
@@ -297,7 +301,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_nn2 = cv.take<int32_t>(N), o_nn3 = cv.take<int32_t>(N), o_d1 = cv.take<float>(N), o_d2 = cv.take<float>(N),
                  o_L = cv.take<float>(N), o_hcell = cv.take<int32_t>(N), o_front = cv.take<int32_t>(N),
                  o_inF = cv.take<uint8_t>(Npad), o_failed = cv.take<uint8_t>(Npad),
-                 o_sflag = cv.take<uint8_t>(Npad), o_brank = cv.take<int2>(N), o_sorted = cv.take<float4>(N),
+                 o_sflag = cv.take<uint8_t>(Npad), o_brank = cv.take<int2>(N), o_sorted = cv.take<float4>(4 * c->n_quads),
                  o_bstart = cv.take<int32_t>(c->n_buckets_pad), o_far = cv.take<int32_t>(N),
                  o_nlogn = cv.take<double>(kNlognTable),
                  o_stage = cv.take<float>(N * c->dim), o_items = cv.take<APItem>(items.size()),
@@ -338,7 +342,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->failed = (uint8_t *)(b + o_failed);
     c->sflag = (uint8_t *)(b + o_sflag);
     c->brank = (int2 *)(b + o_brank);
-    c->sorted = (float4 *)(b + o_sorted);
+    c->squad = (float4 *)(b + o_sorted);
     c->bucket_start = (int32_t *)(b + o_bstart);
     c->far_list = (int32_t *)(b + o_far);
     c->far_count = (int32_t *)(b + o_farc);
@@ -390,6 +394,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
         cudaError_t e3 = cudaMemsetAsync(c->inF, 0, Npad, s);
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->failed, 0, Npad, s);
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->sflag, 0, Npad, s);
+        // quad padding: all-ones bytes are NaN coordinates and index -1
+        if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->squad, 0xff, (size_t)c->n_quads * 4 * sizeof(float4), s);
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->res, 0, S * sizeof(cert_scene_result), s);
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->status, 0, 4 * sizeof(uint32_t), s);
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->fstart, 0, (S + 1) * sizeof(int32_t), s);

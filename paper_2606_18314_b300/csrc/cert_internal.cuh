@@ -37,7 +37,8 @@ struct SceneParams {
     int32_t h_off, g_h;            // entropy grid: cells [h_off, h_off + g_h^dim), g_h per axis
     int32_t ap_off, ap_nch;        // all-pairs partials: base index, chunks per query
     int32_t ap_chunk, g_default;   // all-pairs chunk length; default search resolution
-    int32_t pad0, pad1;
+    int32_t s_off;                 // first slot of the scene in the quad-padded sorted array (multiple of 4)
+    int32_t pad1;
 };
 
 // Per-scene state carried across steps.
@@ -158,6 +159,70 @@ __device__ __forceinline__ void sqdist_qpair(unsigned long long qx, unsigned lon
         D0 = __fadd_rn(D0, z0);
         D1 = __fadd_rn(D1, z1);
     }
+}
+
+// Squared distances of four candidates, held as quad rows X = (x0..x3),
+// Y, Z, to the query whose coordinates are packed twice (px = {x, x}, ...):
+// packed differences and squares, scalar additions in the order of sqdist,
+// so each result equals sqdist<DIM>(query, candidate k) bit for bit.
+template <int DIM>
+__device__ __forceinline__ void sqdist_quad(unsigned long long px, unsigned long long py, unsigned long long pz,
+                                            const float4 X, const float4 Y, const float4 Z, float &D0, float &D1,
+                                            float &D2, float &D3)
+{
+    unsigned long long ax, bx, ay, by;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ax) : "l"(pack2(X.x, X.y)), "l"(px));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(bx) : "l"(pack2(X.z, X.w)), "l"(px));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ay) : "l"(pack2(Y.x, Y.y)), "l"(py));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(by) : "l"(pack2(Y.z, Y.w)), "l"(py));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(ax) : "l"(ax));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(bx) : "l"(bx));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(ay) : "l"(ay));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(by) : "l"(by));
+    float x0, x1, x2, x3, y0, y1, y2, y3;
+    unpack2(ax, x0, x1);
+    unpack2(bx, x2, x3);
+    unpack2(ay, y0, y1);
+    unpack2(by, y2, y3);
+    D0 = __fadd_rn(x0, y0);
+    D1 = __fadd_rn(x1, y1);
+    D2 = __fadd_rn(x2, y2);
+    D3 = __fadd_rn(x3, y3);
+    if (DIM == 3) {
+        unsigned long long az, bz;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(az) : "l"(pack2(Z.x, Z.y)), "l"(pz));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(bz) : "l"(pack2(Z.z, Z.w)), "l"(pz));
+        asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(az) : "l"(az));
+        asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(bz) : "l"(bz));
+        float z0, z1, z2, z3;
+        unpack2(az, z0, z1);
+        unpack2(bz, z2, z3);
+        D0 = __fadd_rn(D0, z0);
+        D1 = __fadd_rn(D1, z1);
+        D2 = __fadd_rn(D2, z2);
+        D3 = __fadd_rn(D3, z3);
+    }
+}
+
+// ----------------------------------------------------------------------------- sorted points
+
+// The points in search-grid order are stored in quads: quad q holds slots
+// 4q .. 4q+3 as four float4 rows (x0..x3), (y0..y3), (z0..z3), (index bits).
+// Every scene starts on a quad (SceneParams::s_off); slots past a scene's end
+// up to the next quad hold NaN coordinates and index -1, so a whole quad can
+// be evaluated and the padding never enters a top-k.
+__device__ __forceinline__ void sorted_store(float4 *quads, int k, float x, float y, float z, int id)
+{
+    float *f = reinterpret_cast<float *>(quads + (size_t)(k >> 2) * 4) + (k & 3);
+    f[0] = x;
+    f[4] = y;
+    f[8] = z;
+    f[12] = __int_as_float(id);
+}
+
+__device__ __forceinline__ int sorted_index(const float4 *quads, int k)
+{
+    return __float_as_int(reinterpret_cast<const float *>(quads + (size_t)(k >> 2) * 4)[12 + (k & 3)]);
 }
 
 // Cell coordinate of one axis: floor(x * g) clamped to [0, g-1].

@@ -33,7 +33,7 @@ struct StepArgs {
     int32_t *bucket_count;         // [n_buckets_pad]
     int32_t *bucket_start;         // [n_buckets_pad]
     int2 *brank;                   // [n] (bucket, rank in bucket)
-    float4 *sorted;                // [n] positions in bucket order, .w = point index bits
+    float4 *squad;                 // points in bucket order, quad layout (sorted_store), padded per scene
     uint8_t *sflag;                // [n_pad] by sorted slot: 1 = search this point
     int32_t *far_list;             // [n] sorted slots left to the far pass
     int32_t *far_count;            // number of entries in far_list (zeroed every call)

@@ -420,12 +420,12 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
         const SceneParams sp = a.sp[s];
         const int2 br = a.brank[i];
         int slot = a.bucket_start[br.x] + br.y;
-        if ((unsigned)slot >= (unsigned)a.n_total) {  // only after a timed-out scan
+        if ((unsigned)(slot - sp.pt_off) >= (unsigned)sp.n) {  // only after a timed-out scan
             atomicOr(a.status, ST_TIMEOUT);
             slot = i;
         }
         const float4 p = a.pos_new[i];
-        a.sorted[slot] = make_float4(p.x, p.y, p.z, __int_as_float(i));
+        sorted_store(a.squad, slot - sp.pt_off + sp.s_off, p.x, p.y, p.z, i);
         bool need = true;
         if (a.mode == MODE_STEP && a.st[s].strategy == STRAT_INC) {
             const int na = a.nn[i], nb = a.nn2[i], nc = a.nn3[i];
@@ -495,42 +495,55 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
 // ============================================================================ k_search
 
 struct SearchCtx {
-    const float4 *sorted;
+    const float4 *squad;
     const int *bstart;
     float4 p;
+    unsigned long long px2, py2, pz2;   // query coordinates, each packed twice
     int gi;
-    int pt_off, n, boff, T;
+    int pt_off, n, pad, boff, T;        // pad = s_off - pt_off (slot -> quad-array index)
     uint32_t mask;
     int g;
     float inv_g;
     bool dense;
 };
 
-// Visit the sorted slots [lo, hi) two candidates at a time; the next pair's
-// loads are issued before the current pair's distances.
+// Visit the sorted slots [lo, hi) of the scene.  The range is widened to whole
+// quads; the extra slots are other points of the same scene (visiting more
+// points never changes a top-k) or NaN padding, which no comparison accepts.
+// Each quad is four 16-byte loads and one packed evaluation, with the next
+// quad's loads issued before the current quad's arithmetic; one test of the
+// quad's minimum against the current fourth key skips the insertions.
 template <int DIM>
 __device__ __forceinline__ void visit_range(const SearchCtx &c, int lo, int hi, Top4 &t)
 {
     lo = max(lo, c.pt_off);          // a bucket range never leaves its scene
     hi = min(hi, c.pt_off + c.n);
     if (lo >= hi) return;
-    float4 n0 = c.sorted[lo];
-    float4 n1 = (lo + 1 < hi) ? c.sorted[lo + 1] : n0;
-    int k = lo;
-    for (; k + 1 < hi; k += 2) {
-        const float4 q0 = n0, q1 = n1;
-        if (k + 2 < hi) n0 = c.sorted[k + 2];
-        if (k + 3 < hi) n1 = c.sorted[k + 3];
-        const int j0 = __float_as_int(q0.w), j1 = __float_as_int(q1.w);
-        float D0, D1;
-        sqdist_pair<DIM>(c.p, q0, q1, D0, D1);
-        if (D0 <= t.d3 && j0 != c.gi) top4_insert(t, D0, j0);
-        if (D1 <= t.d3 && j1 != c.gi) top4_insert(t, D1, j1);
-    }
-    if (k < hi) {   // odd length: n0 holds slot hi - 1
-        const int j = __float_as_int(n0.w);
-        const float D = sqdist<DIM>(c.p, n0);
-        if (D <= t.d3 && j != c.gi) top4_insert(t, D, j);
+    const int q0 = (lo + c.pad) >> 2;
+    const int q1 = (hi + c.pad + 3) >> 2;
+    const float4 *r = c.squad + (size_t)q0 * 4;
+    float4 X = r[0], Y = r[1];
+    float4 Z = (DIM == 3) ? r[2] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = q0; q < q1; ++q) {
+        const float4 cX = X, cY = Y, cZ = Z;
+        const float4 *rc = r;
+        r += 4;
+        if (q + 1 < q1) {
+            X = r[0];
+            Y = r[1];
+            if (DIM == 3) Z = r[2];
+        }
+        float D0, D1, D2, D3;
+        sqdist_quad<DIM>(c.px2, c.py2, c.pz2, cX, cY, cZ, D0, D1, D2, D3);
+        if (fminf(fminf(D0, D1), fminf(D2, D3)) <= t.d3) {
+            const float4 J = rc[3];
+            const int j0 = __float_as_int(J.x), j1 = __float_as_int(J.y);
+            const int j2 = __float_as_int(J.z), j3 = __float_as_int(J.w);
+            if (D0 <= t.d3 && j0 != c.gi) top4_insert(t, D0, j0);
+            if (D1 <= t.d3 && j1 != c.gi) top4_insert(t, D1, j1);
+            if (D2 <= t.d3 && j2 != c.gi) top4_insert(t, D2, j2);
+            if (D3 <= t.d3 && j3 != c.gi) top4_insert(t, D3, j3);
+        }
     }
 }
 
@@ -589,30 +602,28 @@ __device__ __forceinline__ bool grid_search(const SearchCtx &c, Top4 &t, float &
     const int cy = cell_coord(c.p.y, c.g, gf);
     const int cz = (DIM == 3) ? cell_coord(c.p.z, c.g, gf) : 0;
     top4_reset(t);
-    // The 3^d block.  Fetch every row's slot range first (independent loads),
-    // keep them in this thread's column of the shared range table, then walk
-    // all rows as one stream so that a warp runs max(sum of lengths) rather
-    // than sum(max of lengths) iterations.
+    // The 3^d block.  Fetch every row's slot range first (independent loads)
+    // into this thread's column of the shared range table, then walk the rows,
+    // the query's own row first: its nearest candidates set a tight fourth key
+    // early, so most quads of the other rows skip the insertions.
     constexpr int NR = (DIM == 3) ? 9 : 3;
-    int total = 0;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-        const int yr = cy + (k % 3) - 1;
-        const int zr = (DIM == 3) ? cz + (k / 3) - 1 : 0;
+        const int kr = (k + NR / 2) % NR;   // the query's own row first
+        const int yr = cy + (kr % 3) - 1;
+        const int zr = (DIM == 3) ? cz + (kr / 3) - 1 : 0;
         int lo, hi, lo2, hi2;
         row_ranges<DIM>(c, yr, zr, cx - 1, cx + 1, lo, hi, lo2, hi2);
         if (hi2 > lo2) visit_range<DIM>(c, lo2, hi2, t);   // wrapped row: rare
         lo = max(lo, c.pt_off);
         hi = max(lo, min(hi, c.pt_off + c.n));
         rng[k * kThreads] = make_int2(lo, hi);
-        total += hi - lo;
     }
 #pragma unroll 1
     for (int k = 0; k < NR; ++k) {
         const int2 r = rng[k * kThreads];
         visit_range<DIM>(c, r.x, r.y, t);
     }
-    (void)total;
 
     const int gm = c.g - 1;
     int x0 = max(cx - 1, 0), x1 = min(cx + 1, gm);
@@ -748,22 +759,26 @@ __global__ void __launch_bounds__(kThreads) k_search(const StepArgs a)
         SearchOut o = {0, 0, 0, 0.0};
         if (active) {
             const int slot = s_list[e];
-            const float4 q = a.sorted[slot];
-            int gi = __float_as_int(q.w);
-            if ((unsigned)gi >= (unsigned)a.n_total) {  // only after a timed-out scan
+            s = a.scene_of[slot];        // slot ranges of scenes equal their point ranges
+            const SceneParams sp = a.sp[s];
+            const SceneState &st = a.st[s];
+            int gi = sorted_index(a.squad, slot - sp.pt_off + sp.s_off);
+            if ((unsigned)(gi - sp.pt_off) >= (unsigned)sp.n) {  // only after a timed-out scan
                 atomicOr(a.status, ST_TIMEOUT);
                 gi = slot;
             }
-            s = a.scene_of[gi];
-            const SceneParams sp = a.sp[s];
-            const SceneState &st = a.st[s];
+            const float4 q = a.pos_new[gi];
             SearchCtx c;
-            c.sorted = a.sorted;
+            c.squad = a.squad;
             c.bstart = a.bucket_start;
             c.p = q;
+            c.px2 = pack2(q.x, q.x);
+            c.py2 = pack2(q.y, q.y);
+            c.pz2 = pack2(q.z, q.z);
             c.gi = gi;
             c.pt_off = sp.pt_off;
             c.n = sp.n;
+            c.pad = sp.s_off - sp.pt_off;
             c.boff = sp.bucket_off;
             c.T = sp.bucket_mask + 1;
             c.mask = (uint32_t)sp.bucket_mask;
@@ -815,31 +830,29 @@ __global__ void __launch_bounds__(kThreads) k_far(const StepArgs a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int item = blockIdx.x; item < nfar; item += gridDim.x) {
         const int slot = a.far_list[item];
-        const float4 q = a.sorted[slot];
-        int gi = __float_as_int(q.w);
-        if ((unsigned)gi >= (unsigned)a.n_total) gi = slot;
-        const int s = a.scene_of[gi];
+        const int s = a.scene_of[slot];
         const SceneParams sp = a.sp[s];
+        int gi = sorted_index(a.squad, slot - sp.pt_off + sp.s_off);
+        if ((unsigned)(gi - sp.pt_off) >= (unsigned)sp.n) gi = slot;
+        const float4 p = a.pos_new[gi];
+        const unsigned long long px = pack2(p.x, p.x), py = pack2(p.y, p.y), pz = pack2(p.z, p.z);
         Top4 t;
         top4_reset(t);
-        const int end = sp.pt_off + sp.n;
-        int j = sp.pt_off + threadIdx.x;
-        for (; j + 3 * kThreads < end; j += 4 * kThreads) {
-            float4 c[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) c[u] = a.sorted[j + u * kThreads];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int jj = __float_as_int(c[u].w);
-                const float D = sqdist<DIM>(q, c[u]);
-                if (D <= t.d3 && jj != gi) top4_insert(t, D, jj);
-            }
-        }
-        for (; j < end; j += kThreads) {
-            const float4 c = a.sorted[j];
-            const int jj = __float_as_int(c.w);
-            const float D = sqdist<DIM>(q, c);
-            if (D <= t.d3 && jj != gi) top4_insert(t, D, jj);
+        // every quad of the scene, coalesced across the CTA
+        const int q1 = (sp.s_off + sp.n + 3) >> 2;
+        for (int q = (sp.s_off >> 2) + threadIdx.x; q < q1; q += kThreads) {
+            const float4 *r = a.squad + (size_t)q * 4;
+            const float4 X = r[0], Y = r[1];
+            const float4 Z = (DIM == 3) ? r[2] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 J = r[3];
+            float D0, D1, D2, D3;
+            sqdist_quad<DIM>(px, py, pz, X, Y, Z, D0, D1, D2, D3);
+            const int j0 = __float_as_int(J.x), j1 = __float_as_int(J.y);
+            const int j2 = __float_as_int(J.z), j3 = __float_as_int(J.w);
+            if (D0 <= t.d3 && j0 != gi) top4_insert(t, D0, j0);
+            if (D1 <= t.d3 && j1 != gi) top4_insert(t, D1, j1);
+            if (D2 <= t.d3 && j2 != gi) top4_insert(t, D2, j2);
+            if (D3 <= t.d3 && j3 != gi) top4_insert(t, D3, j3);
         }
         warp_merge_top4(t);
         if (lane == 0) {
