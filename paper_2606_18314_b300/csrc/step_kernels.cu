@@ -547,6 +547,58 @@ __device__ __forceinline__ void visit_range(const SearchCtx &c, int lo, int hi, 
     }
 }
 
+
+// Walk the quad ranges rng[0..NR) (column stride kThreads) as one stream, the
+// next quad's loads -- across row ends too -- issued before the current
+// quad's arithmetic.
+template <int DIM, int NR>
+__device__ __forceinline__ void visit_quad_rows(const SearchCtx &c, const int2 *rng, Top4 &t)
+{
+    int k = 0;
+    int2 rr = rng[0];
+    int q = rr.x, qe = rr.y;
+    while (q >= qe && k + 1 < NR) {
+        ++k;
+        rr = rng[k * kThreads];
+        q = rr.x;
+        qe = rr.y;
+    }
+    if (q >= qe) return;
+    const float4 *r = c.squad + (size_t)q * 4;
+    float4 X = r[0], Y = r[1];
+    float4 Z = (DIM == 3) ? r[2] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (;;) {
+        const float4 cX = X, cY = Y, cZ = Z;
+        const float4 *rc = r;
+        ++q;
+        while (q >= qe && k + 1 < NR) {
+            ++k;
+            rr = rng[k * kThreads];
+            q = rr.x;
+            qe = rr.y;
+        }
+        const bool more = q < qe;
+        if (more) {
+            r = c.squad + (size_t)q * 4;
+            X = r[0];
+            Y = r[1];
+            if (DIM == 3) Z = r[2];
+        }
+        float D0, D1, D2, D3;
+        sqdist_quad<DIM>(c.px2, c.py2, c.pz2, cX, cY, cZ, D0, D1, D2, D3);
+        if (fminf(fminf(D0, D1), fminf(D2, D3)) <= t.d3) {
+            const float4 J = rc[3];
+            const int j0 = __float_as_int(J.x), j1 = __float_as_int(J.y);
+            const int j2 = __float_as_int(J.z), j3 = __float_as_int(J.w);
+            if (D0 <= t.d3 && j0 != c.gi) top4_insert(t, D0, j0);
+            if (D1 <= t.d3 && j1 != c.gi) top4_insert(t, D1, j1);
+            if (D2 <= t.d3 && j2 != c.gi) top4_insert(t, D2, j2);
+            if (D3 <= t.d3 && j3 != c.gi) top4_insert(t, D3, j3);
+        }
+        if (!more) break;
+    }
+}
+
 // Slot range(s) of the cells [xl, xh] of row (yr, zr).  A row's cells are
 // consecutive buckets; the second range is non-empty only when they wrap.
 template <int DIM>
@@ -603,9 +655,10 @@ __device__ __forceinline__ bool grid_search(const SearchCtx &c, Top4 &t, float &
     const int cz = (DIM == 3) ? cell_coord(c.p.z, c.g, gf) : 0;
     top4_reset(t);
     // The 3^d block.  Fetch every row's slot range first (independent loads)
-    // into this thread's column of the shared range table, then walk the rows,
-    // the query's own row first: its nearest candidates set a tight fourth key
-    // early, so most quads of the other rows skip the insertions.
+    // and keep it, as a range of quads, in this thread's column of the shared
+    // range table; then walk the rows as one quad stream, the query's own row
+    // first: its nearest candidates set a tight fourth key early, so most
+    // quads of the other rows skip the insertions.
     constexpr int NR = (DIM == 3) ? 9 : 3;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
@@ -616,14 +669,10 @@ __device__ __forceinline__ bool grid_search(const SearchCtx &c, Top4 &t, float &
         row_ranges<DIM>(c, yr, zr, cx - 1, cx + 1, lo, hi, lo2, hi2);
         if (hi2 > lo2) visit_range<DIM>(c, lo2, hi2, t);   // wrapped row: rare
         lo = max(lo, c.pt_off);
-        hi = max(lo, min(hi, c.pt_off + c.n));
-        rng[k * kThreads] = make_int2(lo, hi);
+        hi = min(hi, c.pt_off + c.n);
+        rng[k * kThreads] = (lo < hi) ? make_int2((lo + c.pad) >> 2, (hi + c.pad + 3) >> 2) : make_int2(0, 0);
     }
-#pragma unroll 1
-    for (int k = 0; k < NR; ++k) {
-        const int2 r = rng[k * kThreads];
-        visit_range<DIM>(c, r.x, r.y, t);
-    }
+    visit_quad_rows<DIM, NR>(c, rng, t);
 
     const int gm = c.g - 1;
     int x0 = max(cx - 1, 0), x1 = min(cx + 1, gm);
@@ -733,7 +782,7 @@ __device__ __forceinline__ SearchOut write_certificate(const StepArgs &a, const 
 // (ascending, so a warp's queries are neighbours and share most rows), then
 // searches them kThreads at a time.
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_search(const StepArgs a)
+__global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 64 registers: 4 CTAs per SM
 {
     constexpr int NR = (DIM == 3) ? 9 : 3;
     constexpr int PER = kSearchChunk / kThreads;   // slots per thread in the compaction
