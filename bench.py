@@ -366,7 +366,7 @@ def main():
     if not args.no_autotune:
         idx = [cycle_index(clock[0] + k, F) for k in range(min(8, C))]
         probe = torch.stack([dev_frames[i] for i in idx]).contiguous()
-        scales = (1.5, 2.0, 2.5, 3.0, 4.0)
+        scales = (2.0, 2.5, 3.0, 3.5, 4.0, 5.0)
         best, ms_sc = ctx.autotune(probe, eps, strat if strat != cert.CERT_ALLPAIRS else cert.CERT_INCREMENTAL,
                                    scales)
         tuned = {"scales": list(scales), "ms": [float(x) for x in ms_sc], "best": best}

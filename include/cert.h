@@ -69,7 +69,7 @@ typedef struct {
                                  increasing, every scene >= 3 points, total < 2^31;
                                  NULL allowed when n_scenes == 1 together with n_total */
     int64_t n_total;          /* total points (used when offsets == NULL)             */
-    float cell_scale;         /* search-grid cell side / reference d2 (0 -> 2.5)      */
+    float cell_scale;         /* search-grid cell side / reference d2 (0 -> 3.5)      */
     int32_t policy;           /* strategy for CERT_AUTO without a selector (0 -> INCREMENTAL) */
     int32_t bucket_factor;    /* hashed-grid buckets per scene = factor x next_pow2(n);
                                  1, 2, 4 or 8 (0 -> 1)                                 */

@@ -400,7 +400,7 @@ class Context:
     def restore(self, stream=None):
         _check(lib().cert_restore(self.h, _stream_ptr(stream)), self.h)
 
-    def autotune(self, frames, eps, strategy=CERT_INCREMENTAL, scales=(1.0, 1.25, 1.5, 2.0, 2.5), stream=None):
+    def autotune(self, frames, eps, strategy=CERT_INCREMENTAL, scales=(2.0, 2.5, 3.0, 3.5, 4.0, 5.0), stream=None):
         """cert_autotune over consecutive device frames [F][n][dim]; returns (best, ms per scale)."""
         if isinstance(strategy, str):
             strategy = STRATEGY[strategy]

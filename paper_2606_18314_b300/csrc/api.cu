@@ -20,7 +20,7 @@ using namespace certk;
 struct cert_ctx {
     int dim = 0, S = 0;
     int64_t N = 0;
-    float cell_scale = 2.5f;
+    float cell_scale = 3.5f;
     float cell_quantile = 0.5f;
     int bucket_factor = 1;
     int policy = STRAT_INC;
@@ -245,7 +245,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->dim = cfg->dim;
     c->S = cfg->n_scenes;
     c->N = off.back();
-    c->cell_scale = cfg->cell_scale > 0.0f ? cfg->cell_scale : 2.5f;
+    c->cell_scale = cfg->cell_scale > 0.0f ? cfg->cell_scale : 3.5f;
     c->cell_quantile = cfg->cell_quantile > 0.0f ? cfg->cell_quantile : 0.5f;
     c->bucket_factor = cfg->bucket_factor > 0 ? cfg->bucket_factor : 1;
     c->policy = cfg->policy == STRAT_AUTO ? STRAT_INC : cfg->policy;

@@ -427,8 +427,9 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
         const float4 p = a.pos_new[i];
         sorted_store(a.squad, slot - sp.pt_off + sp.s_off, p.x, p.y, p.z, i);
         bool need = true;
-        if (a.mode == MODE_STEP && a.st[s].strategy == STRAT_INC) {
+        if (a.mode == MODE_STEP) {
             const int na = a.nn[i], nb = a.nn2[i], nc = a.nn3[i];
+            float hint = 0.0f;             // no box hint unless the candidates are valid
             if ((unsigned)na < (unsigned)sp.n && (unsigned)nb < (unsigned)sp.n) {
                 // fresh keys of the three stored candidates, sorted
                 float d1 = sqdist<DIM>(p, a.pos_new[sp.pt_off + na]);
@@ -455,9 +456,13 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
                 // (triangle inequality); both terms rounded up with slack
                 const float shrink = __fmul_ru(__fadd_ru(__fsqrt_ru(p.w), eps_of(a.acc, s)), 1.0f + 0x1p-18f);
                 const float Lnew = __fsub_rd(a.L[i], shrink);
+                // a search of this point can size its box from the second key:
+                // the fresh runner-up over all points is no farther
+                hint = __fsqrt_ru(d2);
                 // every point outside {nn, nn2, nn3} is now at least Lnew away, so
                 // when the second key is closer the top-2 is the first two keys
-                if (Lnew > 0.0f && __fmul_ru(d2, 1.0f + 0x1p-19f) < __fmul_rd(Lnew, Lnew)) {
+                if (a.st[s].strategy == STRAT_INC && Lnew > 0.0f &&
+                    __fmul_ru(d2, 1.0f + 0x1p-19f) < __fmul_rd(Lnew, Lnew)) {
                     need = false;
                     a.nn[i] = j1;
                     a.nn2[i] = j2;
@@ -475,6 +480,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
                     }
                 }
             }
+            if (need) a.L[i] = hint;       // read by the search; replaced by its result
         }
         a.sflag[slot] = need ? 1 : 0;
     }
@@ -551,8 +557,8 @@ __device__ __forceinline__ void visit_range(const SearchCtx &c, int lo, int hi, 
 // Walk the quad ranges rng[0..NR) (column stride kThreads) as one stream, the
 // next quad's loads -- across row ends too -- issued before the current
 // quad's arithmetic.
-template <int DIM, int NR>
-__device__ __forceinline__ void visit_quad_rows(const SearchCtx &c, const int2 *rng, Top4 &t)
+template <int DIM>
+__device__ __forceinline__ void visit_quad_rows(const SearchCtx &c, const int2 *rng, int NR, Top4 &t)
 {
     int k = 0;
     int2 rr = rng[0];
@@ -637,6 +643,8 @@ __device__ __forceinline__ void visit_row(const SearchCtx &c, int yr, int zr, in
 }
 
 constexpr float kFaceSlack = 0x1p-17f;   // >> FP error of cell assignment and face position
+constexpr float kHintGrow = 1.15f;       // box radius / box hint (margin for the bound L)
+constexpr int kMaxRows = 16;             // rows of a hinted box kept in the shared range table
 
 // Thread-level grid search over a box of cells [x0,x1] x [y0,y1] x [z0,z1]
 // holding the query's cell.  It starts as the 3^d block of Algorithm 1 and
@@ -647,37 +655,72 @@ constexpr float kFaceSlack = 0x1p-17f;   // >> FP error of cell assignment and f
 // Returns false after kMaxExtend layers; such a query is appended to the far
 // list and finished by k_far.
 template <int DIM>
-__device__ __forceinline__ bool grid_search(const SearchCtx &c, Top4 &t, float &Lout, int2 *rng)
+__device__ __forceinline__ bool grid_search(const SearchCtx &c, Top4 &t, float &Lout, int2 *rng, float hint)
 {
     const float gf = (float)c.g;
     const int cx = cell_coord(c.p.x, c.g, gf);
     const int cy = cell_coord(c.p.y, c.g, gf);
     const int cz = (DIM == 3) ? cell_coord(c.p.z, c.g, gf) : 0;
-    top4_reset(t);
-    // The 3^d block.  Fetch every row's slot range first (independent loads)
-    // and keep it, as a range of quads, in this thread's column of the shared
-    // range table; then walk the rows as one quad stream, the query's own row
-    // first: its nearest candidates set a tight fourth key early, so most
-    // quads of the other rows skip the insertions.
-    constexpr int NR = (DIM == 3) ? 9 : 3;
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-        const int kr = (k + NR / 2) % NR;   // the query's own row first
-        const int yr = cy + (kr % 3) - 1;
-        const int zr = (DIM == 3) ? cz + (kr / 3) - 1 : 0;
-        int lo, hi, lo2, hi2;
-        row_ranges<DIM>(c, yr, zr, cx - 1, cx + 1, lo, hi, lo2, hi2);
-        if (hi2 > lo2) visit_range<DIM>(c, lo2, hi2, t);   // wrapped row: rare
-        lo = max(lo, c.pt_off);
-        hi = min(hi, c.pt_off + c.n);
-        rng[k * kThreads] = (lo < hi) ? make_int2((lo + c.pad) >> 2, (hi + c.pad + 3) >> 2) : make_int2(0, 0);
-    }
-    visit_quad_rows<DIM, NR>(c, rng, t);
-
     const int gm = c.g - 1;
-    int x0 = max(cx - 1, 0), x1 = min(cx + 1, gm);
-    int y0 = max(cy - 1, 0), y1 = min(cy + 1, gm);
-    int z0 = (DIM == 3) ? max(cz - 1, 0) : 0, z1 = (DIM == 3) ? min(cz + 1, gm) : 0;
+    top4_reset(t);
+    // Every row's slot range is fetched first (independent loads) and kept, as
+    // a range of quads, in this thread's column of the shared range table; the
+    // rows are then walked as one quad stream, the query's own row first: its
+    // nearest candidates set a tight fourth key early, so most quads of the
+    // other rows skip the insertions.
+    int x0, x1, y0, y1, z0, z1, nrows = 0;
+    if (hint > 0.0f) {
+        // The box of the cells that meet the ball of radius kHintGrow * hint:
+        // the runner-up is at most hint away, so the enclosure test nearly
+        // always passes without growing the box.
+        const float R = __fmul_ru(hint, kHintGrow);
+        x0 = cell_coord(__fsub_rd(c.p.x, R), c.g, gf);
+        x1 = cell_coord(__fadd_ru(c.p.x, R), c.g, gf);
+        y0 = cell_coord(__fsub_rd(c.p.y, R), c.g, gf);
+        y1 = cell_coord(__fadd_ru(c.p.y, R), c.g, gf);
+        z0 = (DIM == 3) ? cell_coord(__fsub_rd(c.p.z, R), c.g, gf) : 0;
+        z1 = (DIM == 3) ? cell_coord(__fadd_ru(c.p.z, R), c.g, gf) : 0;
+        if ((y1 - y0 + 1) * (z1 - z0 + 1) <= kMaxRows) {
+            rng[0] = make_int2(0, 0);      // the own row's entry, filled in the loop
+            nrows = 1;
+            for (int z = z0; z <= z1; ++z)
+                for (int y = y0; y <= y1; ++y) {
+                    const int k = (y == cy && z == cz) ? 0 : nrows++;
+                    int lo, hi, lo2, hi2;
+                    row_ranges<DIM>(c, y, z, x0, x1, lo, hi, lo2, hi2);
+                    if (hi2 > lo2) visit_range<DIM>(c, lo2, hi2, t);   // wrapped row: rare
+                    lo = max(lo, c.pt_off);
+                    hi = min(hi, c.pt_off + c.n);
+                    rng[k * kThreads] = (lo < hi) ? make_int2((lo + c.pad) >> 2, (hi + c.pad + 3) >> 2)
+                                                  : make_int2(0, 0);
+                }
+        }
+    }
+    if (nrows == 0) {
+        // no usable hint: the 3^d block of Algorithm 1
+        constexpr int NR = (DIM == 3) ? 9 : 3;
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const int kr = (k + NR / 2) % NR;   // the query's own row first
+            const int yr = cy + (kr % 3) - 1;
+            const int zr = (DIM == 3) ? cz + (kr / 3) - 1 : 0;
+            int lo, hi, lo2, hi2;
+            row_ranges<DIM>(c, yr, zr, cx - 1, cx + 1, lo, hi, lo2, hi2);
+            if (hi2 > lo2) visit_range<DIM>(c, lo2, hi2, t);   // wrapped row: rare
+            lo = max(lo, c.pt_off);
+            hi = min(hi, c.pt_off + c.n);
+            rng[k * kThreads] = (lo < hi) ? make_int2((lo + c.pad) >> 2, (hi + c.pad + 3) >> 2) : make_int2(0, 0);
+        }
+        nrows = NR;
+        x0 = max(cx - 1, 0);
+        x1 = min(cx + 1, gm);
+        y0 = max(cy - 1, 0);
+        y1 = min(cy + 1, gm);
+        z0 = (DIM == 3) ? max(cz - 1, 0) : 0;
+        z1 = (DIM == 3) ? min(cz + 1, gm) : 0;
+    }
+    visit_quad_rows<DIM>(c, rng, nrows, t);
+
     const float inf = __int_as_float(0x7f800000);
     for (int ext = 0;; ++ext) {
         // distances to the six faces (+inf on the grid edge)
@@ -789,7 +832,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
     static_assert(PER == 4, "the flag load below reads four flags at once");
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ int s_list[kSearchChunk];
-    __shared__ int2 s_rng[NR * kThreads];          // per-thread row ranges, column-major
+    __shared__ int2 s_rng[(kMaxRows > NR ? kMaxRows : NR) * kThreads];   // per-thread row ranges, column-major
     const int base = blockIdx.x * kSearchChunk + threadIdx.x * PER;
     // flags beyond n_total are zero up to the padded length (a multiple of the chunk)
     const uint32_t fw = (base < a.n_total) ? *reinterpret_cast<const uint32_t *>(a.sflag + base) : 0u;
@@ -836,7 +879,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
             c.dense = grid_is_dense<DIM>(c.g, c.T);
             Top4 t;
             float L;
-            if (grid_search<DIM>(c, t, L, s_rng + threadIdx.x))
+            const float hint = (a.mode == MODE_STEP) ? a.L[gi] : 0.0f;   // written by the refresh
+            if (grid_search<DIM>(c, t, L, s_rng + threadIdx.x, hint))
                 o = write_certificate(a, sp, gi, t, L);
             else
                 a.far_list[atomicAdd(a.far_count, 1)] = slot;   // finished by k_far
