@@ -138,6 +138,22 @@ cert_status cert_step(cert_ctx *ctx, const float *d_pos_new, float eps, int32_t 
 cert_status cert_step_host(cert_ctx *ctx, const float *h_pos_new, float eps, int32_t strategy,
                            cert_scene_result *h_scenes, void *stream);
 
+/* n_steps consecutive steps from HOST frames, with the host-to-device copies
+ * pipelined against the steps.  h_frames[k] is step k's positions,
+ * [n_total][dim] float32 (pinned for full speed); the pointer table itself is
+ * read on the host.  h_scenes should be pinned too: a copy into pageable
+ * memory returns only when the step is done, which stops the overlap.
+ * Frame k+1 is copied on the context's own copy stream,
+ * into the other of two device staging buffers, while step k runs on
+ * `stream`; each step then copies its per-scene scalars to
+ * h_scenes[k * n_scenes ...] (may be NULL).  Results equal n_steps calls of
+ * cert_step_host.  Synchronises `stream` before returning.  Creates the copy
+ * stream and its events on first use; allocates no device memory.  Errors:
+ * CERT_EINVAL for a NULL table or frame, or n_steps < 0; CERT_ECUDA for a
+ * failed copy or launch. */
+cert_status cert_step_host_stream(cert_ctx *ctx, const float *const *h_frames, int32_t n_steps, float eps,
+                                  int32_t strategy, cert_scene_result *h_scenes, void *stream);
+
 /* Recompute every certificate of the current positions by a full grid search
  * (the O(N) rebuild of Sec. 3).  Step outputs (frontier, failures, H) keep the
  * values of the last step. */

@@ -64,7 +64,7 @@ class cert_views(ctypes.Structure):
 _lib = None
 
 # every symbol include/cert.h declares (checked by the CPU tests)
-EXPORTS = ["cert_init", "cert_step", "cert_step_host", "cert_rebuild", "cert_get_views",
+EXPORTS = ["cert_init", "cert_step", "cert_step_host", "cert_step_host_stream", "cert_rebuild", "cert_get_views",
            "cert_sync_result", "cert_distances", "cert_allpairs", "cert_destroy", "cert_last_error",
            "cert_version", "cert_profile_begin", "cert_profile_end",
            "cert_allpairs_noalloc", "cert_set_cell_scale", "cert_set_cell_quantile", "cert_get_cell_scale", "cert_autotune",
@@ -88,6 +88,8 @@ def lib():
     L.cert_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(cert_config), vp, vp]
     L.cert_step.argtypes = [vp, vp, f32, i32, ctypes.POINTER(cert_views), vp]
     L.cert_step_host.argtypes = [vp, vp, f32, i32, vp, vp]
+    L.cert_step_host_stream.argtypes = [vp, vp, i32, f32, i32, vp, vp]
+    L.cert_step_host_stream.restype = ctypes.c_int
     L.cert_rebuild.argtypes = [vp, vp]
     L.cert_get_views.argtypes = [vp, ctypes.POINTER(cert_views)]
     L.cert_sync_result.argtypes = [vp, vp]
@@ -339,6 +341,19 @@ class Context:
         """cert_step_host on a raw (pinned) host pointer; ``out`` receives the scalars."""
         _check(lib().cert_step_host(self.h, ctypes.c_void_p(host_ptr), float(eps), int(strategy),
                                     ctypes.c_void_p(out.ctypes.data), _stream_ptr(stream)), self.h)
+
+    def step_host_stream(self, host_ptrs, eps, strategy, out: np.ndarray, stream=None):
+        """cert_step_host_stream: one step per (pinned) host frame pointer in
+        host_ptrs, copies pipelined against the steps; ``out``
+        [len(host_ptrs) * n_scenes] receives each step's scalars."""
+        n_steps = len(host_ptrs)
+        if out is not None and out.size < n_steps * self.n_scenes:
+            raise ValueError("out holds fewer than n_steps * n_scenes results")
+        table = (ctypes.c_void_p * max(1, n_steps))(*[int(p) for p in host_ptrs])
+        _check(lib().cert_step_host_stream(self.h, ctypes.cast(table, ctypes.c_void_p), int(n_steps), float(eps),
+                                           int(strategy),
+                                           ctypes.c_void_p(out.ctypes.data) if out is not None else None,
+                                           _stream_ptr(stream)), self.h)
 
     def rebuild(self, stream=None):
         _check(lib().cert_rebuild(self.h, _stream_ptr(stream)), self.h)

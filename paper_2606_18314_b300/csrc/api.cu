@@ -57,6 +57,10 @@ struct cert_ctx {
     float *feat = nullptr;          // [S][8] selector features of the last step
     // snapshot of the mutable state (allocated by the first cert_snapshot)
     char *snap = nullptr;
+    // pipelined host steps: a second staging buffer, a copy stream and events (created on first use)
+    float *stage2 = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
     size_t snap_bytes = 0;
     int snap_cur = 0;
     bool snap_valid = false;
@@ -304,7 +308,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_sflag = cv.take<uint8_t>(Npad), o_brank = cv.take<int2>(N), o_sorted = cv.take<float4>(4 * c->n_quads),
                  o_bstart = cv.take<int32_t>(c->n_buckets_pad), o_far = cv.take<int32_t>(N),
                  o_nlogn = cv.take<double>(kNlognTable),
-                 o_stage = cv.take<float>(N * c->dim), o_items = cv.take<APItem>(items.size()),
+                 o_stage = cv.take<float>(N * c->dim), o_stage2 = cv.take<float>(N * c->dim), o_items = cv.take<APItem>(items.size()),
                  o_pd = cv.take<float>(3 * apoff), o_pj = cv.take<int32_t>(3 * apoff),
                  o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16), o_feat = cv.take<float>(S * 8);
     cv.off = (cv.off + 255) & ~size_t(255);
@@ -348,6 +352,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->far_count = (int32_t *)(b + o_farc);
     c->nlogn = (double *)(b + o_nlogn);
     c->stage = (float *)(b + o_stage);
+    c->stage2 = (float *)(b + o_stage2);
     c->ap_items = (APItem *)(b + o_items);
     c->ap_pd = (float *)(b + o_pd);
     c->ap_pj = (int32_t *)(b + o_pj);
@@ -487,6 +492,45 @@ cert_status cert_step_host(cert_ctx *c, const float *h_pos_new, float eps, int32
     if (h_scenes)
         CK(c, cudaMemcpyAsync(h_scenes, c->res, size_t(c->S) * sizeof(cert_scene_result),
                               cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    return CERT_OK;
+}
+
+cert_status cert_step_host_stream(cert_ctx *c, const float *const *h_frames, int32_t n_steps, float eps,
+                                  int32_t strategy, cert_scene_result *h_scenes, void *stream)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    if (!h_frames) return fail(c, CERT_EINVAL, "frames are NULL");
+    if (n_steps < 0) return fail(c, CERT_EINVAL, "n_steps < 0");
+    for (int32_t k = 0; k < n_steps; ++k)
+        if (!h_frames[k]) return fail(c, CERT_EINVAL, "a frame pointer is NULL");
+    const int64_t frame = c->N * c->dim;
+    if (!c->copy_stream) {
+        CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            CK(c, cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
+            CK(c, cudaEventCreateWithFlags(&c->ev_used[k], cudaEventDisableTiming));
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float *buf[2] = {c->stage, c->stage2};
+    // both buffers are free once the caller's stream has reached this point
+    for (int k = 0; k < 2; ++k) CK(c, cudaEventRecord(c->ev_used[k], s));
+    for (int32_t k = 0; k < n_steps; ++k) {
+        const int b = k & 1;
+        // copy frame k while step k-1 runs; buffer b was last read by step k-2
+        CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_used[b], 0));
+        CK(c, cudaMemcpyAsync(buf[b], h_frames[k], size_t(frame) * sizeof(float),
+                              cudaMemcpyHostToDevice, c->copy_stream));
+        CK(c, cudaEventRecord(c->ev_copied[b], c->copy_stream));
+        CK(c, cudaStreamWaitEvent(s, c->ev_copied[b], 0));
+        const cert_status rc = cert_step(c, buf[b], eps, strategy, nullptr, stream);
+        if (rc != CERT_OK) return rc;
+        CK(c, cudaEventRecord(c->ev_used[b], s));
+        if (h_scenes)
+            CK(c, cudaMemcpyAsync(h_scenes + (size_t)k * c->S, c->res, size_t(c->S) * sizeof(cert_scene_result),
+                                  cudaMemcpyDeviceToHost, s));
+    }
     CK(c, cudaStreamSynchronize(s));
     return CERT_OK;
 }
@@ -716,6 +760,11 @@ void cert_destroy(cert_ctx *c)
     if (!c) return;
     cudaDeviceSynchronize();
     if (c->snap) cudaFree(c->snap);
+    for (int k = 0; k < 2; ++k) {
+        if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+        if (c->ev_used[k]) cudaEventDestroy(c->ev_used[k]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     cudaFree(c->blob);
     delete c;

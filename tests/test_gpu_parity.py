@@ -310,3 +310,36 @@ def test_distances_and_host_step(torch):
     r = oracle.step(p, q, ref)
     assert int(out[0]["n_failed"]) == r.n_failed and int(out[0]["n_frontier"]) == len(r.frontier)
     assert abs(float(out[0]["H"]) - r.H) <= H_TOL
+
+
+def test_pipelined_host_steps_match_the_oracle(torch):
+    """cert_step_host_stream: frames copied on the context's copy stream into
+    two staging buffers while the previous step runs.  Every step's scalars
+    and the final certificates equal the oracle's, and the frame table may
+    revisit frames (a ping-pong cycle)."""
+    from paper_2606_18314_b300 import cert
+    bm = scenes.BatchMotion.mixed(n_scenes=6, lo=500, hi=3000, eps=2e-3, seed=21)
+    off = bm.offsets
+    fr = bm.frames(4)
+    host_frames = torch.from_numpy(fr).pin_memory()
+    ctx = cert.Context(dev(torch, fr[0]), offsets=off)
+    order = [1, 2, 3, 4, 3, 2]
+    row = fr[0].size * 4
+    out = np.zeros(len(order) * (len(off) - 1), cert.SCENE_DTYPE)
+    ctx.step_host_stream([host_frames.data_ptr() + k * row for k in order], 2e-3, cert.CERT_INCREMENTAL, out)
+    prev = [oracle.top2(fr[0][off[s]:off[s + 1]]) for s in range(len(off) - 1)]
+    for step, k in enumerate(order):
+        for s in range(len(off) - 1):
+            cur = fr[k][off[s]:off[s + 1]]
+            r = oracle.step(fr[order[step - 1] if step else 0][off[s]:off[s + 1]], cur, prev[s])
+            sc = out[step * (len(off) - 1) + s]
+            assert int(sc["n_failed"]) == r.n_failed and int(sc["n_frontier"]) == len(r.frontier), (step, s)
+            assert abs(float(sc["H"]) - r.H) <= H_TOL, (step, s)
+            assert int(sc["n_missed"]) == 0
+            prev[s] = r.cert
+    v = ctx.views()
+    for s in range(len(off) - 1):
+        assert np.array_equal(host(v["nn"])[off[s]:off[s + 1]], prev[s].nn)
+        assert np.array_equal(host(v["d2sq"])[off[s]:off[s + 1]].view(np.uint32), prev[s].d2sq.view(np.uint32))
+    with pytest.raises(cert.CertError):
+        ctx.step_host_stream([0], 2e-3, cert.CERT_INCREMENTAL, None)
