@@ -38,62 +38,87 @@ namespace certk {
 
 // ============================================================================ k_prepare
 
+// kPrepPer points per thread (strided by kThreads, so a warp's lanes still hold
+// consecutive points): the loads, atomics and stores of the points are issued
+// together, overlapping their latencies.
+constexpr int kPrepPer = 4;
+
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_prepare(const StepArgs a)
 {
-    const int i = blockIdx.x * kThreads + threadIdx.x;
-    const bool valid = i < a.n_total;
-    int s = -1;
-    unsigned dbits = 0u;
-    int first = 0;
-    if (valid) {
-        s = a.scene_of[i];
-        const SceneParams sp = a.sp[s];
-        float4 p;
-        if (a.mode == MODE_REBUILD) {
-            p = a.pos_new[i];
-        } else {
-            const float *q = a.pos_in + (size_t)i * DIM;
-            p.x = q[0];
-            p.y = q[1];
-            p.z = (DIM == 3) ? q[2] : 0.0f;
-            p.w = 0.0f;
-            if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) atomicOr(a.status, ST_NONFINITE);
+    const int base = blockIdx.x * (kThreads * kPrepPer) + threadIdx.x;
+    int s[kPrepPer];
+    float4 p[kPrepPer], po[kPrepPer];
+#pragma unroll
+    for (int k = 0; k < kPrepPer; ++k) {
+        const int i = base + k * kThreads;
+        s[k] = -1;
+        p[k] = po[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < a.n_total) {
+            s[k] = a.scene_of[i];
+            if (a.mode == MODE_REBUILD) {
+                p[k] = a.pos_new[i];
+            } else {
+                const float *q = a.pos_in + (size_t)i * DIM;
+                p[k].x = q[0];
+                p[k].y = q[1];
+                p[k].z = (DIM == 3) ? q[2] : 0.0f;
+                if (a.mode == MODE_STEP) po[k] = a.pos_old[i];
+            }
+        }
+    }
+    unsigned dbits[kPrepPer];
+    int first[kPrepPer], rank[kPrepPer], b[kPrepPer], hc[kPrepPer];
+#pragma unroll
+    for (int k = 0; k < kPrepPer; ++k) {
+        const int i = base + k * kThreads;
+        dbits[k] = 0u;
+        first[k] = 0;
+        if (s[k] < 0) continue;
+        if (a.mode != MODE_REBUILD) {
+            if (!(isfinite(p[k].x) && isfinite(p[k].y) && isfinite(p[k].z))) atomicOr(a.status, ST_NONFINITE);
             if (a.mode == MODE_STEP) {
                 // squared displacement of this point; kept in w for the refresh
-                const float D = sqdist<DIM>(a.pos_old[i], p);
-                dbits = (D >= 0.0f) ? __float_as_uint(D) : 0u;
-                p.w = D;
+                const float D = sqdist<DIM>(po[k], p[k]);
+                dbits[k] = (D >= 0.0f) ? __float_as_uint(D) : 0u;
+                p[k].w = D;
             }
-            a.pos_new[i] = p;
+            a.pos_new[i] = p[k];
         }
+        const SceneParams sp = a.sp[s[k]];
         // hashed search grid: bucket of the cell, rank inside the bucket
-        const int g = a.st[s].g_cur;
+        const int g = a.st[s[k]].g_cur;
         const float gf = (float)g;
-        const int cx = cell_coord(p.x, g, gf);
-        const int cy = cell_coord(p.y, g, gf);
-        const int cz = (DIM == 3) ? cell_coord(p.z, g, gf) : 0;
+        const int cx = cell_coord(p[k].x, g, gf);
+        const int cy = cell_coord(p[k].y, g, gf);
+        const int cz = (DIM == 3) ? cell_coord(p[k].z, g, gf) : 0;
         const bool dense = grid_is_dense<DIM>(g, sp.bucket_mask + 1);
-        const int b = sp.bucket_off + (int)((row_base<DIM>(cy, cz, g, dense) + (uint32_t)cx) & (uint32_t)sp.bucket_mask);
-        const int rank = atomicAdd(&a.bucket_count[b], 1);
-        a.brank[i] = make_int2(b, rank);
+        b[k] = sp.bucket_off + (int)((row_base<DIM>(cy, cz, g, dense) + (uint32_t)cx) & (uint32_t)sp.bucket_mask);
+        rank[k] = atomicAdd(&a.bucket_count[b[k]], 1);
         // entropy grid on the post-step position (Def. 2)
         if (a.mode != MODE_REBUILD) {
             const int gh = sp.g_h;
             const float ghf = (float)gh;
-            const int hx = cell_coord(p.x, gh, ghf);
-            const int hy = cell_coord(p.y, gh, ghf);
-            const int hc = (DIM == 3) ? (cell_coord(p.z, gh, ghf) * gh + hy) * gh + hx : hy * gh + hx;
-            a.hcell[i] = hc;
-            first = atomicAdd(&a.hocc[sp.h_off + hc], 1) == 0;
+            const int hx = cell_coord(p[k].x, gh, ghf);
+            const int hy = cell_coord(p[k].y, gh, ghf);
+            hc[k] = (DIM == 3) ? (cell_coord(p[k].z, gh, ghf) * gh + hy) * gh + hx : hy * gh + hx;
+            first[k] = atomicAdd(&a.hocc[sp.h_off + hc[k]], 1) == 0;
         }
     }
-    const unsigned m = scene_run_mask(s);
-    const unsigned mx = run_max_u32(m, dbits);
-    const int occ = run_sum_i32(m, first);
-    if (s >= 0 && run_leader(m)) {
-        if (mx) atomicMax(&a.acc[s].eps_bits, mx);
-        if (occ) atomicAdd(&a.acc[s].occ, occ);
+#pragma unroll
+    for (int k = 0; k < kPrepPer; ++k) {
+        const int i = base + k * kThreads;
+        if (s[k] >= 0) {
+            a.brank[i] = make_int2(b[k], rank[k]);
+            if (a.mode != MODE_REBUILD) a.hcell[i] = hc[k];
+        }
+        const unsigned m = scene_run_mask(s[k]);
+        const unsigned mx = run_max_u32(m, dbits[k]);
+        const int occ = run_sum_i32(m, first[k]);
+        if (s[k] >= 0 && run_leader(m)) {
+            if (mx) atomicMax(&a.acc[s[k]].eps_bits, mx);
+            if (occ) atomicAdd(&a.acc[s[k]].occ, occ);
+        }
     }
 }
 
@@ -153,13 +178,18 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     if (t < a.ntiles_b) {
         // ---- bucket counts -> bucket starts (global exclusive scan over all scenes)
         const int base = t * kScanTile + threadIdx.x * kScanItems;
-        const int4 c0 = *reinterpret_cast<const int4 *>(a.bucket_count + base);
-        const int4 c1 = *reinterpret_cast<const int4 *>(a.bucket_count + base + 4);
-        const uint32_t v[8] = {(uint32_t)c0.x, (uint32_t)c0.y, (uint32_t)c0.z, (uint32_t)c0.w,
-                               (uint32_t)c1.x, (uint32_t)c1.y, (uint32_t)c1.z, (uint32_t)c1.w};
+        uint32_t v[kScanItems];
+#pragma unroll
+        for (int k = 0; k < kScanItems; k += 4) {
+            const int4 c4 = *reinterpret_cast<const int4 *>(a.bucket_count + base + k);
+            v[k] = (uint32_t)c4.x;
+            v[k + 1] = (uint32_t)c4.y;
+            v[k + 2] = (uint32_t)c4.z;
+            v[k + 3] = (uint32_t)c4.w;
+        }
         uint32_t sum = 0u;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sum += v[k];
+        for (int k = 0; k < kScanItems; ++k) sum += v[k];
         uint32_t tot;
         const uint32_t pre = block_exclusive_scan(sum, &tot, s_warp);
         if (threadIdx.x < 32) {
@@ -168,25 +198,26 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
         }
         __syncthreads();
         uint32_t run = s_excl + pre;
-        int o[8];
+        int o[kScanItems];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < kScanItems; ++k) {
             o[k] = (int)run;
             run += v[k];
         }
-        *reinterpret_cast<int4 *>(a.bucket_start + base) = make_int4(o[0], o[1], o[2], o[3]);
-        *reinterpret_cast<int4 *>(a.bucket_start + base + 4) = make_int4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+        for (int k = 0; k < kScanItems; k += 4)
+            *reinterpret_cast<int4 *>(a.bucket_start + base + k) = make_int4(o[k], o[k + 1], o[k + 2], o[k + 3]);
         return;
     }
 
     // ---- frontier flags -> ascending frontier list (Algorithm 1, Lemma 1)
     const int tp = t - a.ntiles_b;
     const int base = tp * kScanTile + threadIdx.x * kScanItems;
-    uint32_t f[8];
-    int sc[8];
+    uint32_t f[kScanItems];
+    int sc[kScanItems];
     uint32_t sum = 0u;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kScanItems; ++k) {
         const int i = base + k;
         f[k] = 0u;
         sc[k] = -1;
@@ -212,12 +243,12 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     }
     __syncthreads();
     uint32_t run = s_excl + pre;
-    // a thread's 8 consecutive points nearly always share one scene: accumulate
-    // locally and reduce once per warp; a scene change inside the 8 is flushed directly
+    // a thread's consecutive points nearly always share one scene: accumulate
+    // locally and reduce once per warp; a scene change inside them is flushed directly
     int cur = -1, acc_first = 0;
     double acc_dl = 0.0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kScanItems; ++k) {
         const int i = base + k;
         const int s = sc[k];
         if (s >= 0) {
@@ -408,38 +439,64 @@ __global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
 
 // ============================================================================ k_scatter_refresh
 
+// kScatPer points per thread (strided by kThreads), their loads issued together.
+constexpr int kScatPer = 2;
+
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
 {
-    const int i = blockIdx.x * kThreads + threadIdx.x;
-    const bool valid = i < a.n_total;
-    int s = -1, changed = 0, missed = 0, first = 0;
-    double dl = 0.0;
-    if (valid) {
-        s = a.scene_of[i];
-        const SceneParams sp = a.sp[s];
-        const int2 br = a.brank[i];
-        int slot = a.bucket_start[br.x] + br.y;
+    const int base = blockIdx.x * (kThreads * kScatPer) + threadIdx.x;
+    const bool step = a.mode == MODE_STEP;
+    int s[kScatPer], na[kScatPer], nb[kScatPer], nc[kScatPer];
+    int2 br[kScatPer];
+    float4 p[kScatPer];
+    float Lold[kScatPer];
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k) {
+        const int i = base + k * kThreads;
+        s[k] = -1;
+        na[k] = nb[k] = nc[k] = -1;
+        Lold[k] = 0.0f;
+        if (i < a.n_total) {
+            s[k] = a.scene_of[i];
+            br[k] = a.brank[i];
+            p[k] = a.pos_new[i];
+            if (step) {
+                na[k] = a.nn[i];
+                nb[k] = a.nn2[i];
+                nc[k] = a.nn3[i];
+                Lold[k] = a.L[i];
+            }
+        }
+    }
+    int changed[kScatPer], missed[kScatPer], first[kScatPer];
+    double dl[kScatPer];
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k) {
+        const int i = base + k * kThreads;
+        changed[k] = missed[k] = first[k] = 0;
+        dl[k] = 0.0;
+        if (s[k] < 0) continue;
+        const SceneParams sp = a.sp[s[k]];
+        int slot = a.bucket_start[br[k].x] + br[k].y;
         if ((unsigned)(slot - sp.pt_off) >= (unsigned)sp.n) {  // only after a timed-out scan
             atomicOr(a.status, ST_TIMEOUT);
             slot = i;
         }
-        const float4 p = a.pos_new[i];
-        sorted_store(a.squad, slot - sp.pt_off + sp.s_off, p.x, p.y, p.z, i);
+        sorted_store(a.squad, slot - sp.pt_off + sp.s_off, p[k].x, p[k].y, p[k].z, i);
         bool need = true;
-        if (a.mode == MODE_STEP) {
-            const int na = a.nn[i], nb = a.nn2[i], nc = a.nn3[i];
+        if (step) {
             float hint = 0.0f;             // no box hint unless the candidates are valid
-            if ((unsigned)na < (unsigned)sp.n && (unsigned)nb < (unsigned)sp.n) {
+            if ((unsigned)na[k] < (unsigned)sp.n && (unsigned)nb[k] < (unsigned)sp.n) {
                 // fresh keys of the three stored candidates, sorted
-                float d1 = sqdist<DIM>(p, a.pos_new[sp.pt_off + na]);
-                float d2 = sqdist<DIM>(p, a.pos_new[sp.pt_off + nb]);
-                float d3 = __int_as_float(0x7f800000);
-                int j1 = na, j2 = nb, j3 = 0x7fffffff;
-                if ((unsigned)nc < (unsigned)sp.n) {
-                    d3 = sqdist<DIM>(p, a.pos_new[sp.pt_off + nc]);
-                    j3 = nc;
-                }
+                const bool hc3 = (unsigned)nc[k] < (unsigned)sp.n;
+                const float4 qa = a.pos_new[sp.pt_off + na[k]];
+                const float4 qb = a.pos_new[sp.pt_off + nb[k]];
+                const float4 qc = hc3 ? a.pos_new[sp.pt_off + nc[k]] : qa;
+                float d1 = sqdist<DIM>(p[k], qa);
+                float d2 = sqdist<DIM>(p[k], qb);
+                float d3 = hc3 ? sqdist<DIM>(p[k], qc) : __int_as_float(0x7f800000);
+                int j1 = na[k], j2 = nb[k], j3 = hc3 ? nc[k] : 0x7fffffff;
                 if (key_less(d2, j2, d1, j1)) {
                     swapv(d1, d2);
                     swapv(j1, j2);
@@ -454,14 +511,14 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
                 }
                 // any distance from i changed by at most |p'_i - p_i| + eps_t
                 // (triangle inequality); both terms rounded up with slack
-                const float shrink = __fmul_ru(__fadd_ru(__fsqrt_ru(p.w), eps_of(a.acc, s)), 1.0f + 0x1p-18f);
-                const float Lnew = __fsub_rd(a.L[i], shrink);
+                const float shrink = __fmul_ru(__fadd_ru(__fsqrt_ru(p[k].w), eps_of(a.acc, s[k])), 1.0f + 0x1p-18f);
+                const float Lnew = __fsub_rd(Lold[k], shrink);
                 // a search of this point can size its box from the second key:
                 // the fresh runner-up over all points is no farther
                 hint = __fsqrt_ru(d2);
                 // every point outside {nn, nn2, nn3} is now at least Lnew away, so
                 // when the second key is closer the top-2 is the first two keys
-                if (a.st[s].strategy == STRAT_INC && Lnew > 0.0f &&
+                if (a.st[s[k]].strategy == STRAT_INC && Lnew > 0.0f &&
                     __fmul_ru(d2, 1.0f + 0x1p-19f) < __fmul_rd(Lnew, Lnew)) {
                     need = false;
                     a.nn[i] = j1;
@@ -470,13 +527,13 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
                     a.d1sq[i] = d1;
                     a.d2sq[i] = d2;
                     a.L[i] = Lnew;
-                    changed = j1 != na;
-                    a.failed[i] = (uint8_t)changed;
-                    if (changed) {
-                        missed = !a.inF[i];
+                    changed[k] = j1 != na[k];
+                    a.failed[i] = (uint8_t)changed[k];
+                    if (changed[k]) {
+                        missed[k] = !a.inF[i];
                         const int old = atomicAdd(&a.hfail[sp.h_off + a.hcell[i]], 1);
-                        first = old == 0;
-                        dl = nlogn_step(a.nlogn, old);
+                        first[k] = old == 0;
+                        dl[k] = nlogn_step(a.nlogn, old);
                     }
                 }
             }
@@ -484,17 +541,22 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
         }
         a.sflag[slot] = need ? 1 : 0;
     }
-    if (a.mode != MODE_STEP) return;  // uniform across the grid
-    const unsigned m = scene_run_mask(s);
-    const int nc = run_sum_i32(m, changed);
-    const int nm = run_sum_i32(m, missed);
-    const int fc = run_sum_i32(m, first);
-    const double sd = run_sum_f64(m, dl);
-    if (s >= 0 && run_leader(m) && nc) {
-        atomicAdd(&a.acc[s].n_failed, nc);
-        atomicAdd(&a.acc[s].n_missed, nm);
-        atomicAdd(&a.acc[s].failed_cells, fc);
-        atomicAdd(&a.acc[s].s_fail, sd);
+    if (!step) return;  // uniform across the grid
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k) {
+        const unsigned m = scene_run_mask(s[k]);
+        const int ncg = run_sum_i32(m, changed[k]);
+        if (__any_sync(kFull, ncg != 0)) {
+            const int nm = run_sum_i32(m, missed[k]);
+            const int fc = run_sum_i32(m, first[k]);
+            const double sd = run_sum_f64(m, dl[k]);
+            if (s[k] >= 0 && run_leader(m) && ncg) {
+                atomicAdd(&a.acc[s[k]].n_failed, ncg);
+                atomicAdd(&a.acc[s[k]].n_missed, nm);
+                atomicAdd(&a.acc[s[k]].failed_cells, fc);
+                atomicAdd(&a.acc[s[k]].s_fail, sd);
+            }
+        }
     }
 }
 
@@ -1038,10 +1100,10 @@ template <int DIM>
 static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
 {
     switch (phase) {
-    case PH_PREPARE: k_prepare<DIM><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(a); break;
+    case PH_PREPARE: k_prepare<DIM><<<nblk(a.n_total, kThreads * kPrepPer), kThreads, 0, st>>>(a); break;
     case PH_SCAN: k_scan<DIM><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a); break;
     case PH_SELECT: k_select<DIM><<<a.n_scenes, kThreads, 0, st>>>(a); break;
-    case PH_SCATTER: k_scatter_refresh<DIM><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(a); break;
+    case PH_SCATTER: k_scatter_refresh<DIM><<<nblk(a.n_total, kThreads * kScatPer), kThreads, 0, st>>>(a); break;
     case PH_SEARCH:
         k_search<DIM><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
         if (cudaPeekAtLastError() == cudaSuccess) k_far<DIM><<<kFarCtas, kThreads, 0, st>>>(a);
