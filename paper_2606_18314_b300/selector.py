@@ -13,6 +13,9 @@ It never changes a certificate, only which exact strategy runs.
 * Network: MLP 8-64-64-2, ReLU, MSE on the log times, Adam.  Forward, backward
   and Adam all run in the library's kernels (``cert_mlp_*``); this module only
   slices minibatches and moves arrays.
+* Decision: incremental when ln t_inc - ln t_reb <= delta, the margin with the
+  least regret on the training rows (``decision_margin``), folded into the
+  rebuild head's bias so the in-loop argmin applies it.
 
 CLI (on a GPU):
     python -m paper_2606_18314_b300.selector collect --out labels.npz [--seeds 16]
@@ -188,6 +191,27 @@ def regret(T_ln, choose_inc):
     return float((chosen - best).sum() / best.sum())
 
 
+def decision_margin(Y, T):
+    """The margin delta of the rule 'incremental when pred_inc - pred_reb <= delta'
+    with the least regret on the given rows (measured times T).  With the rows
+    sorted by their predicted difference, choosing incremental on the first k
+    rows costs the prefix sum of t_inc plus the suffix sum of t_reb; every k is
+    tried and the cheapest taken (ties to the larger k: more incremental
+    steps).  The margin is folded into the rebuild head's bias, so the
+    device's argmin applies it unchanged."""
+    diff = (Y[:, 0] - Y[:, 1]).astype(np.float64)
+    t = np.exp(T.astype(np.float64))
+    order = np.argsort(diff, kind="stable")
+    d, ti, tr = diff[order], t[order, 0], t[order, 1]
+    cost = np.concatenate([[0.0], np.cumsum(ti)]) + np.concatenate([np.cumsum(tr[::-1])[::-1], [0.0]])
+    k = int(len(cost) - 1 - np.argmin(cost[::-1]))          # last minimum: the most incremental rows
+    if k == 0:
+        return float(d[0] - 1.0)
+    if k == len(d):
+        return float(d[-1] + 1.0)
+    return float(0.5 * (d[k - 1] + d[k]))
+
+
 def load(path=WEIGHTS):
     d = np.load(path)
     return d["params"].astype(np.float32), d["norm"].astype(np.float32)
@@ -220,10 +244,13 @@ def main():
     trn = Trainer(X[tr], T[tr], seed=args.seed)
     hist = trn.fit(epochs=args.epochs)
     params, norm = trn.params_np(), trn.norm_np
+    delta = decision_margin(predict(params, norm, X[tr]), T[tr])
+    params[-1] += np.float32(delta)     # fold the margin into the rebuild head's bias
     Yv = predict(params, norm, X[val])
-    vloss = float(np.mean((Yv - T[val]) ** 2))
+    vloss = float(np.mean((Yv[:, 0] - T[val, 0]) ** 2 + (Yv[:, 1] - delta - T[val, 1]) ** 2) / 2)
     learned = Yv[:, 0] <= Yv[:, 1]
     meta = {"rows": int(len(X)), "train_rows": int(len(tr)), "val_rows": int(nval), "epochs": args.epochs,
+            "decision_margin": float(delta),
             "train_loss_first": hist[0], "train_loss_last": hist[-1], "val_mse": vloss,
             "val_regret_learned": regret(T[val], learned),
             "val_regret_always_incremental": regret(T[val], np.ones(nval, bool)),
