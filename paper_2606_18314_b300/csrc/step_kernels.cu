@@ -322,9 +322,9 @@ __global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ int s_bin;
     __shared__ float s_feat[8];
-    __shared__ float s_h1[64];
-    __shared__ float s_h2[64];
-    __shared__ float s_out[4];
+    __shared__ __align__(16) float s_h1[64];
+    __shared__ __align__(16) float s_h2[64];
+    __shared__ float s_out[2];
     const int s = blockIdx.x;
     const SceneParams sp = a.sp[s];
     const int ns = min(sp.n, kMedianSample);
@@ -382,35 +382,58 @@ __global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
             __syncthreads();
             const float *W1 = a.sel_params, *b1 = W1 + 64 * 8, *W2 = b1 + 64, *b2 = W2 + 64 * 64,
                         *W3 = b2 + 64, *b3 = W3 + 2 * 64;
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
             if (threadIdx.x < 64) {
+                const float4 wa = *reinterpret_cast<const float4 *>(W1 + threadIdx.x * 8);
+                const float4 wb = *reinterpret_cast<const float4 *>(W1 + threadIdx.x * 8 + 4);
                 float z = b1[threadIdx.x];
-                for (int k = 0; k < 8; ++k) z = fmaf(W1[threadIdx.x * 8 + k], s_feat[k], z);
+                z = fmaf(wa.x, s_feat[0], z);
+                z = fmaf(wa.y, s_feat[1], z);
+                z = fmaf(wa.z, s_feat[2], z);
+                z = fmaf(wa.w, s_feat[3], z);
+                z = fmaf(wb.x, s_feat[4], z);
+                z = fmaf(wb.y, s_feat[5], z);
+                z = fmaf(wb.z, s_feat[6], z);
+                z = fmaf(wb.w, s_feat[7], z);
                 s_h1[threadIdx.x] = fmaxf(z, 0.0f);
             }
             __syncthreads();
-            if (threadIdx.x < 64) {
-                float z = b2[threadIdx.x];
-                for (int k = 0; k < 64; ++k) z = fmaf(W2[threadIdx.x * 64 + k], s_h1[k], z);
-                s_h2[threadIdx.x] = fmaxf(z, 0.0f);
+            {
+                // layer 2 as a warp-cooperative product: warp w owns outputs 8w .. 8w+7,
+                // lane l reads the row pair (2l, 2l+1), coalesced, then the warp reduces
+                const float2 h = *reinterpret_cast<const float2 *>(s_h1 + 2 * lane);
+                float z[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float2 w = *reinterpret_cast<const float2 *>(W2 + (warp * 8 + u) * 64 + 2 * lane);
+                    z[u] = fmaf(w.x, h.x, w.y * h.y);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) z[u] += __shfl_xor_sync(kFull, z[u], o);
+                if (lane < 8) {
+                    float v = z[0];
+#pragma unroll
+                    for (int u = 1; u < 8; ++u)
+                        if (lane == u) v = z[u];
+                    s_h2[warp * 8 + lane] = fmaxf(v + b2[warp * 8 + lane], 0.0f);
+                }
             }
             __syncthreads();
-            if (threadIdx.x < 64) {
-                float y0 = W3[threadIdx.x] * s_h2[threadIdx.x];
-                float y1 = W3[64 + threadIdx.x] * s_h2[threadIdx.x];
+            if (warp < 2) {
+                // output o = warp: lane l covers hidden units (2l, 2l+1)
+                const float2 w = *reinterpret_cast<const float2 *>(W3 + warp * 64 + 2 * lane);
+                const float2 h = *reinterpret_cast<const float2 *>(s_h2 + 2 * lane);
+                float y = fmaf(w.x, h.x, w.y * h.y);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    y0 += __shfl_xor_sync(kFull, y0, o);
-                    y1 += __shfl_xor_sync(kFull, y1, o);
-                }
-                if ((threadIdx.x & 31) == 0) {
-                    s_out[threadIdx.x >> 5] = y0;     // partial sums of the two warps
-                    s_out[2 + (threadIdx.x >> 5)] = y1;
-                }
+                for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(kFull, y, o);
+                if (lane == 0) s_out[warp] = y;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
-                const float pi = s_out[0] + s_out[1] + b3[0];
-                const float pr = s_out[2] + s_out[3] + b3[1];
+                const float pi = s_out[0] + b3[0];
+                const float pr = s_out[1] + b3[1];
                 SceneState st = a.st[s];
                 st.pred_inc = pi;
                 st.pred_reb = pr;
