@@ -301,6 +301,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--prof-steps", type=int, default=200)
     ap.add_argument("--regret-steps", type=int, default=32)
+    ap.add_argument("--rule-steps", type=int, default=32, help="steps per frontier rule in the detection report")
     ap.add_argument("--compare-steps", type=int, default=256)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -442,6 +443,26 @@ def main():
         regret["reference"] = "per step min(incremental, rebuild) on identical state, CUDA events"
         to_cycle_start()
 
+    # ---- the frontier rules (detection only; certificates are exact under each):
+    # Algorithm 1's c <= 4 eps_t, the per-point budget c <= 2 (delta_i + eps_t),
+    # the cumulative clock 4 (S - S_i) >= c^rev_i
+    rules = None
+    if args.rule_steps > 0:
+        rules = {}
+        for rule in ("step", "point", "clock"):
+            c3 = cert.Context(dev_frames[0], offsets=offsets, frontier_rule=rule, cell_scale=ctx.cell_scale())
+            tot = np.zeros(4)
+            for k in range(1, args.rule_steps + 1):
+                c3.step(dev_frames[cycle_index(k, F)], eps, cert.CERT_INCREMENTAL)
+                r, _ = c3.sync(raise_on_status=False)
+                tot += [r["n_frontier"].sum(), r["n_failed"].sum(), r["n_false"].sum(), r["n_missed"].sum()]
+            c3.close()
+            rules[rule] = {"detected_frac": float(tot[0] / (N * args.rule_steps)),
+                           "failed_frac": float(tot[1] / (N * args.rule_steps)),
+                           "false_revalidation": float(tot[2] / max(1.0, tot[0])), "missed": int(tot[3])}
+            assert tot[3] == 0, f"frontier rule {rule} missed a failure"
+        rules["steps"] = args.rule_steps
+
     # ---- per-phase timing (CUDA events on the launching stream), same workload, eager
     P = max(1, args.prof_steps)
     ctx.profile_begin(P)
@@ -541,7 +562,8 @@ def main():
                 "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
-                "step_counts": step_counts, "compare": compare, "regret": regret, "allpairs": allpairs,
+                "step_counts": step_counts, "compare": compare, "regret": regret, "frontier_rules": rules,
+                "allpairs": allpairs,
                 "status": cert.STATUS_NAMES[rc] if 0 <= rc < len(cert.STATUS_NAMES) else rc}
         print(json.dumps(line), flush=True)
     ctx.close()

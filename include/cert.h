@@ -59,6 +59,28 @@ typedef enum {
                              (Prop. 1 with the boundary P ~ 1/log N of Sec. 4)       */
 } cert_strategy;
 
+/* Which points a step flags as its detected frontier F_t (the audit, H_cand and
+ * the selector features use F_t; the certificates are exact under every rule).
+ * Each rule carries the rounding guard tau_i = 2^-20 ((d1_i + d2_i) + x), with x
+ * the rule's motion term, and none ever misses a failed certificate.
+ *   CERT_FRONTIER_STEP   c_i <= 4 eps_t + tau_i (Algorithm 1, Lemma 1), the default.
+ *   CERT_FRONTIER_POINT  c_i <= 2 (delta_i + eps_t) + tau_i with delta_i = |p'_i - p_i|:
+ *                        Lemma 1's triangle inequality with point i's own
+ *                        displacement, the per-point motion budget of Sec. 5.
+ *   CERT_FRONTIER_CLOCK  the cumulative clock of the per-step cost subsection
+ *                        (Thm A.3): S = sum of eps_t in FP64; a certificate last
+ *                        revisited at clock S_i with clearance c^rev_i stays valid
+ *                        while 4 (S - S_i) < c^rev_i, so F_t = {i : c^rev_i <=
+ *                        4 (S - S_i) + 2^-20 ((d1 + d2)^rev_i + (S - S_i))}, in FP64;
+ *                        the points of F_t are revisited (S_i, c^rev_i reset from
+ *                        their post-step certificates).  cert_init and
+ *                        cert_rebuild revisit every point. */
+typedef enum {
+    CERT_FRONTIER_STEP = 0,
+    CERT_FRONTIER_POINT = 1,
+    CERT_FRONTIER_CLOCK = 2
+} cert_frontier_rule;
+
 /* Batch description.  One context holds n_scenes independent scenes whose
  * points are concatenated in scene order: scene s owns points
  * offsets[s] .. offsets[s+1]-1 of every position / result array. */
@@ -75,7 +97,8 @@ typedef struct {
                                  1, 2, 4 or 8 (0 -> 1)                                 */
     float cell_quantile;      /* reference d2 = this quantile of a scene's previous d2
                                  over its first min(n,1024) points, in (0,1] (0 -> 0.5) */
-    int32_t reserved[2];      /* must be zero                                          */
+    int32_t frontier_rule;    /* cert_frontier_rule (0 -> CERT_FRONTIER_STEP)          */
+    int32_t reserved;         /* must be zero                                          */
 } cert_config;
 
 /* Per-scene scalars of the last step.  Same layout on device and host. */

@@ -13,6 +13,11 @@ Nearest-Neighbour Structures"):
 * ``eps`` -- maximum step, Algorithm 1 (first statement).
 * ``frontier`` -- candidate frontier c_i <= 4 eps (+ rounding guard),
   Algorithm 1 (second statement), Lemma 1.
+* ``frontier_point`` -- the per-point motion budget c_i <= 2 (delta_i + eps)
+  (+ guard), the remark closing Sec. 5; ``disp`` gives delta_i.
+* ``ClockState`` -- the cumulative clock of the per-step cost subsection
+  (Thm A.3): a certificate last revisited at clock S_i with clearance c^rev_i
+  stays valid while 4 (S - S_i) < c^rev_i.
 * ``grid_res`` / ``cells`` / ``entropy`` -- index cells, C and H(F_t), Def. 2.
 * ``step`` -- one maintenance step end to end (Algorithm 1 with every
   certificate recomputed from scratch, which is the exact result Cor. A.2 says
@@ -66,6 +71,10 @@ def lib():
         L.oracle_eps.restype = ctypes.c_float
         L.oracle_frontier.argtypes = [f32p, f32p, ctypes.c_int64, ctypes.c_float, ctypes.c_int, i32p]
         L.oracle_frontier.restype = ctypes.c_int64
+        L.oracle_disp.argtypes = [f32p, f32p, ctypes.c_int64, ctypes.c_int, f32p]
+        L.oracle_disp.restype = None
+        L.oracle_frontier_point.argtypes = [f32p, f32p, f32p, ctypes.c_int64, ctypes.c_float, i32p]
+        L.oracle_frontier_point.restype = ctypes.c_int64
         L.oracle_grid_res.argtypes = [ctypes.c_int64, ctypes.c_int]
         L.oracle_grid_res.restype = ctypes.c_int
         L.oracle_cells.argtypes = [f32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, i32p]
@@ -151,6 +160,63 @@ def frontier(d1sq, d2sq, eps_t, guard: bool = True) -> np.ndarray:
     return out[:k].copy()
 
 
+def disp(p_old, p_new) -> np.ndarray:
+    """Per-point displacement delta_i = sqrtf(|p'_i - p_i|^2), FP32."""
+    a, b = _pos(p_old), _pos(p_new)
+    out = np.empty(a.shape[0], np.float32)
+    lib().oracle_disp(_p(a, ctypes.c_float), _p(b, ctypes.c_float), a.shape[0], a.shape[1],
+                      _p(out, ctypes.c_float))
+    return out
+
+
+def frontier_point(d1sq, d2sq, delta, eps_t) -> np.ndarray:
+    """Ascending frontier {i : c_i <= 2 (delta_i + eps_t) + tau_i} (per-point budget)."""
+    d1 = np.ascontiguousarray(d1sq, dtype=np.float32)
+    d2 = np.ascontiguousarray(d2sq, dtype=np.float32)
+    dl = np.ascontiguousarray(delta, dtype=np.float32)
+    out = np.empty(d1.shape[0], np.int32)
+    k = lib().oracle_frontier_point(_p(d1, ctypes.c_float), _p(d2, ctypes.c_float), _p(dl, ctypes.c_float),
+                                    d1.shape[0], float(eps_t), _p(out, ctypes.c_int32))
+    return out[:k].copy()
+
+
+class ClockState:
+    """Cumulative-clock frontier (the per-step cost subsection, Thm A.3): S is
+    the running sum of eps_t in FP64.  A certificate last revisited at clock
+    S_i with clearance c^rev_i (and d1 + d2 = g^rev_i, FP32) stays valid while
+    4 (S - S_i) < c^rev_i; the step's frontier is {i : c^rev_i <= 4 D + 2^-20
+    (g^rev_i + D)}, D = S - S_i, all in FP64 in this order.  After the step the
+    frontier's points are revisited from their post-step certificates."""
+
+    def __init__(self, cert: Certificates):
+        n = cert.nn.shape[0]
+        self.S = 0.0
+        self.S_i = np.zeros(n, np.float64)
+        self._revisit(cert, np.ones(n, bool))
+
+    def _revisit(self, cert: Certificates, who: np.ndarray):
+        d1 = np.sqrt(cert.d1sq).astype(np.float32)
+        d2 = np.sqrt(cert.d2sq).astype(np.float32)
+        if not hasattr(self, "c_rev"):
+            self.c_rev = np.zeros(d1.shape[0], np.float32)
+            self.g_rev = np.zeros(d1.shape[0], np.float32)
+        self.S_i[who] = self.S
+        self.c_rev[who] = (d2 - d1)[who]
+        self.g_rev[who] = (d1 + d2)[who]
+
+    def frontier(self, eps_t) -> np.ndarray:
+        S_t = self.S + float(np.float32(eps_t))
+        D = S_t - self.S_i
+        rhs = 4.0 * D + 2.0 ** -20 * (self.g_rev.astype(np.float64) + D)
+        return np.nonzero(self.c_rev.astype(np.float64) <= rhs)[0].astype(np.int32)
+
+    def advance(self, eps_t, frontier: np.ndarray, cert_new: Certificates):
+        self.S = self.S + float(np.float32(eps_t))
+        who = np.zeros(self.S_i.shape[0], bool)
+        who[frontier] = True
+        self._revisit(cert_new, who)
+
+
 def grid_res(n: int, dim: int) -> int:
     """Entropy-grid cells per axis: smallest g with g^dim >= n (Sec. 2)."""
     return int(lib().oracle_grid_res(int(n), int(dim)))
@@ -216,15 +282,27 @@ def clearances(cert: Certificates) -> np.ndarray:
     return (np.sqrt(cert.d2sq) - np.sqrt(cert.d1sq)).astype(np.float32)
 
 
-def step(p_old, p_new, cert_old: Certificates, nthreads: int = 0) -> StepResult:
+def step(p_old, p_new, cert_old: Certificates, nthreads: int = 0, rule: str = "step",
+         clock: "ClockState | None" = None) -> StepResult:
     """One maintenance step: eps_t, the detected frontier from the pre-step
     certificates, exact post-step certificates, true failures, cells, H and the
-    audit (Algorithm 1; Def. 2; Cor. A.2; Table 1 columns)."""
+    audit (Algorithm 1; Def. 2; Cor. A.2; Table 1 columns).  rule: "step"
+    (Algorithm 1), "point" (per-point budget) or "clock" (cumulative clock,
+    state in ``clock``, advanced here)."""
     p_old, p_new = _pos(p_old), _pos(p_new)
     n, dim = p_new.shape
     e = eps(p_old, p_new)
-    F = frontier(cert_old.d1sq, cert_old.d2sq, e)
+    if rule == "step":
+        F = frontier(cert_old.d1sq, cert_old.d2sq, e)
+    elif rule == "point":
+        F = frontier_point(cert_old.d1sq, cert_old.d2sq, disp(p_old, p_new), e)
+    elif rule == "clock":
+        F = clock.frontier(e)
+    else:
+        raise ValueError(f"unknown frontier rule {rule!r}")
     new = top2(p_new, nthreads)
+    if rule == "clock":
+        clock.advance(e, F, new)
     failed = new.nn != cert_old.nn
     g = grid_res(n, dim)
     cell = cells(p_new, g)

@@ -160,6 +160,39 @@ int64_t oracle_frontier(const float *d1sq, const float *d2sq, int64_t n, float e
     return k;
 }
 
+/*
+ * Per-point displacement delta_i = sqrtf(|p'_i - p_i|^2), the squared distance
+ * in the fixed order above (new minus old).
+ */
+void oracle_disp(const float *p_old, const float *p_new, int64_t n, int dim, float *out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        out[i] = sqrtf(sq_dist(p_old + i * dim, p_new + i * dim, dim));
+}
+
+/*
+ * Frontier under the per-point motion budget (the remark closing Sec. 5 on
+ * the validity radius): nn_i can change only if some other point gets closer
+ * than nn_i; each distance from i changes by at most delta_i + delta_j <=
+ * delta_i + eps (triangle inequality, as in Lemma 1), so the certificate is
+ * safe when c_i > 2 (delta_i + eps).  Same rounding guard as oracle_frontier.
+ */
+int64_t oracle_frontier_point(const float *d1sq, const float *d2sq, const float *disp, int64_t n, float eps,
+                              int32_t *out)
+{
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        float d1 = sqrtf(d1sq[i]);
+        float d2 = sqrtf(d2sq[i]);
+        float c = d2 - d1;
+        float tau = 0x1p-20f * ((d1 + d2) + eps);
+        float rhs = 2.0f * (disp[i] + eps) + tau;
+        if (c <= rhs)
+            out[k++] = (int32_t)i;
+    }
+    return k;
+}
+
 /* Cells per axis of the entropy grid: the smallest g with g^dim >= n, so the
  * mean occupancy is at most a small constant (Sec. 2, first paragraph). */
 int oracle_grid_res(int64_t n, int dim)

@@ -30,7 +30,7 @@ class cert_config(ctypes.Structure):
                 ("offsets", ctypes.POINTER(ctypes.c_int64)), ("n_total", ctypes.c_int64),
                 ("cell_scale", ctypes.c_float), ("policy", ctypes.c_int32),
                 ("bucket_factor", ctypes.c_int32), ("cell_quantile", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("frontier_rule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class cert_scene_result(ctypes.Structure):
@@ -72,6 +72,8 @@ EXPORTS = ["cert_init", "cert_step", "cert_step_host", "cert_step_host_stream", 
            "cert_mlp_workspace_bytes", "cert_mlp_forward", "cert_mlp_grad", "cert_mlp_adam",
            "cert_selftest_bounded_wait"]
 MLP_PARAMS = 4866
+CERT_FRONTIER_STEP, CERT_FRONTIER_POINT, CERT_FRONTIER_CLOCK = 0, 1, 2
+FRONTIER_RULE = {"step": CERT_FRONTIER_STEP, "point": CERT_FRONTIER_POINT, "clock": CERT_FRONTIER_CLOCK}
 N_PHASES = 7
 PHASE_NAMES = ["clear", "prepare", "scan", "select", "scatter_refresh", "search", "finalize"]
 
@@ -278,7 +280,7 @@ class Context:
     """
 
     def __init__(self, pos, offsets=None, cell_scale=0.0, policy=CERT_INCREMENTAL, stream=None,
-                 bucket_factor=0, cell_quantile=0.0):
+                 bucket_factor=0, cell_quantile=0.0, frontier_rule="step"):
         import torch
         self.dim = int(pos.shape[1])
         self._keep = []
@@ -295,6 +297,7 @@ class Context:
         cfg.policy = int(policy)
         cfg.bucket_factor = int(bucket_factor)
         cfg.cell_quantile = float(cell_quantile)
+        cfg.frontier_rule = FRONTIER_RULE[frontier_rule] if isinstance(frontier_rule, str) else int(frontier_rule)
         self.n_scenes = cfg.n_scenes
         self.n = cfg.n_total
         h = ctypes.c_void_p()

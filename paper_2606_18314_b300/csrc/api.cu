@@ -24,6 +24,9 @@ struct cert_ctx {
     float cell_quantile = 0.5f;
     int bucket_factor = 1;
     int policy = STRAT_INC;
+    int frontier_rule = CERT_FRONTIER_STEP;
+    double *clk_s = nullptr;       // cumulative-clock rule: S_i, c^rev_i, (d1 + d2)^rev_i per point
+    float *clk_c = nullptr, *clk_g = nullptr;
     std::vector<SceneParams> h_sp;
     int n_buckets = 0, n_buckets_pad = 0, ntiles_b = 0, ntiles_p = 0;
     int64_t n_h = 0, ap_P = 0;
@@ -182,6 +185,10 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.nlogn = c->nlogn;
     a.res = c->res;
     a.policy = c->policy;
+    a.frontier_rule = c->frontier_rule;
+    a.clk_s = c->clk_s;
+    a.clk_c = c->clk_c;
+    a.clk_g = c->clk_g;
     a.cell_scale = c->cell_scale;
     a.cell_quantile = c->cell_quantile;
     a.sel_params = c->have_sel ? c->sel_params : nullptr;
@@ -204,6 +211,9 @@ static cert_status run_full(cert_ctx *c, int mode, const float *pos_in, cudaStre
     CK(c, launch_step_phase(a, PH_SEARCH, s));
     CK(c, launch_step_phase(a, PH_SELECT, s));
     CK(c, launch_step_phase(a, PH_FINALIZE, s));
+    // clock rule: every certificate was just recomputed, so the next step's scan
+    // revisits every point (resets S_i, c^rev_i and (d1 + d2)^rev_i)
+    if (c->frontier_rule == CERT_FRONTIER_CLOCK) CK(c, cudaMemsetAsync(c->inF, 1, size_t(c->N), s));
     c->last = s;
     return CERT_OK;
 }
@@ -222,8 +232,9 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     if (!d_pos) return fail(nullptr, CERT_EINVAL, "positions are NULL");
     if (cfg->dim != 2 && cfg->dim != 3) return fail(nullptr, CERT_EINVAL, "dim must be 2 or 3");
     if (cfg->n_scenes < 1) return fail(nullptr, CERT_EINVAL, "n_scenes must be >= 1");
-    for (int k = 0; k < 2; ++k)
-        if (cfg->reserved[k]) return fail(nullptr, CERT_EINVAL, "reserved fields must be zero");
+    if (cfg->reserved) return fail(nullptr, CERT_EINVAL, "reserved field must be zero");
+    if (cfg->frontier_rule < CERT_FRONTIER_STEP || cfg->frontier_rule > CERT_FRONTIER_CLOCK)
+        return fail(nullptr, CERT_EINVAL, "unknown frontier_rule");
     if (cfg->bucket_factor != 0 && cfg->bucket_factor != 1 && cfg->bucket_factor != 2 && cfg->bucket_factor != 4 &&
         cfg->bucket_factor != 8)
         return fail(nullptr, CERT_EINVAL, "bucket_factor must be 0, 1, 2, 4 or 8");
@@ -253,6 +264,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->cell_quantile = cfg->cell_quantile > 0.0f ? cfg->cell_quantile : 0.5f;
     c->bucket_factor = cfg->bucket_factor > 0 ? cfg->bucket_factor : 1;
     c->policy = cfg->policy == STRAT_AUTO ? STRAT_INC : cfg->policy;
+    c->frontier_rule = cfg->frontier_rule;
     cudaStream_t s = (cudaStream_t)stream;
 
     // ---- per-scene layout
@@ -311,6 +323,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_stage = cv.take<float>(N * c->dim), o_stage2 = cv.take<float>(N * c->dim), o_items = cv.take<APItem>(items.size()),
                  o_pd = cv.take<float>(3 * apoff), o_pj = cv.take<int32_t>(3 * apoff),
                  o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16), o_feat = cv.take<float>(S * 8);
+    const int64_t Nclk = (c->frontier_rule == CERT_FRONTIER_CLOCK) ? N : 0;
+    const size_t o_clks = cv.take<double>(Nclk), o_clkc = cv.take<float>(Nclk), o_clkg = cv.take<float>(Nclk);
     cv.off = (cv.off + 255) & ~size_t(255);
     const size_t zero_begin = cv.off;
     const size_t o_acc = cv.take<SceneAcc>(S), o_ctr = cv.take<uint32_t>(4), o_farc = cv.take<int32_t>(4),
@@ -359,6 +373,11 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->sel_params = (float *)(b + o_selp);
     c->sel_norm = (float *)(b + o_seln);
     c->feat = (float *)(b + o_feat);
+    if (Nclk) {
+        c->clk_s = (double *)(b + o_clks);
+        c->clk_c = (float *)(b + o_clkc);
+        c->clk_g = (float *)(b + o_clkg);
+    }
     c->zero = b + zero_begin;
     c->acc = (SceneAcc *)(b + o_acc);
     c->tile_ctr = (uint32_t *)(b + o_ctr);
@@ -667,7 +686,9 @@ static std::vector<std::pair<void *, size_t>> snapshot_pieces(cert_ctx *c)
             {c->d1sq, N * 4},                      {c->d2sq, N * 4},       {c->L, N * 4},
             {c->st, S * sizeof(SceneState)},      {c->res, S * sizeof(cert_scene_result)},
             {c->hcell, N * 4},                     {c->frontier, N * 4},   {c->fstart, (S + 1) * 4},
-            {c->failed, N},                        {c->inF, N},            {c->feat, S * 8 * 4}};
+            {c->failed, N},                        {c->inF, N},            {c->feat, S * 8 * 4},
+            {c->clk_s, c->clk_s ? N * 8 : 0},      {c->clk_c, c->clk_c ? N * 4 : 0},
+            {c->clk_g, c->clk_g ? N * 4 : 0}};
 }
 
 cert_status cert_snapshot(cert_ctx *c, void *stream)
@@ -684,6 +705,7 @@ cert_status cert_snapshot(cert_ctx *c, void *stream)
     }
     size_t off = 0;
     for (auto &p : pieces) {
+        if (!p.second) continue;
         CK(c, cudaMemcpyAsync(c->snap + off, p.first, p.second, cudaMemcpyDeviceToDevice, s));
         off += (p.second + 255) & ~size_t(255);
     }
@@ -702,6 +724,7 @@ cert_status cert_restore(cert_ctx *c, void *stream)
     auto pieces = snapshot_pieces(c);
     size_t off = 0;
     for (auto &p : pieces) {
+        if (!p.second) continue;
         CK(c, cudaMemcpyAsync(p.first, c->snap + off, p.second, cudaMemcpyDeviceToDevice, s));
         off += (p.second + 255) & ~size_t(255);
     }

@@ -52,6 +52,7 @@ struct SceneState {
     float pred_inc, pred_reb;
     float inv_g;                   // 1/g_cur, rounded to nearest (face positions of the search)
     int32_t pad0;
+    double S;                      // cumulative clock: sum of the steps' eps_t (FP64)
 };
 
 // Per-scene accumulators, zeroed at the start of every step.

@@ -38,6 +38,9 @@ struct StepArgs {
     int32_t *far_list;             // [n] sorted slots left to the far pass
     int32_t *far_count;            // number of entries in far_list (zeroed every call)
     // certificates
+    int frontier_rule;             // cert_frontier_rule
+    double *clk_s;                 // clock rule, per point: clock of the last revisit
+    float *clk_c, *clk_g;          // ... and c, d1 + d2 of the certificate then
     int32_t *nn, *nn2, *nn3;       // nearest, runner-up, third stored candidate (-1: none)
     float *d1sq, *d2sq, *L;        // L: lower bound on the distance to every other point
     // step outputs

@@ -228,9 +228,38 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
             const float d1 = __fsqrt_rn(a.d1sq[i]);
             const float d2 = __fsqrt_rn(a.d2sq[i]);
             const float c = __fsub_rn(d2, d1);
-            const float tau = __fmul_rn(0x1p-20f, __fadd_rn(__fadd_rn(d1, d2), eps));
-            const float rhs = __fadd_rn(__fmul_rn(4.0f, eps), tau);
-            f[k] = (c <= rhs) ? 1u : 0u;
+            if (a.frontier_rule == CERT_FRONTIER_CLOCK) {
+                // cumulative clock (Thm A.3): revisit last step's frontier from the
+                // current certificates, then test 4 (S - S_i) against c^rev_i, in FP64
+                const double S_prev = a.st[s].S;
+                double S_i;
+                float c_rev, g_rev;
+                if (a.inF[i]) {
+                    S_i = S_prev;
+                    c_rev = c;
+                    g_rev = __fadd_rn(d1, d2);
+                    a.clk_s[i] = S_i;
+                    a.clk_c[i] = c_rev;
+                    a.clk_g[i] = g_rev;
+                } else {
+                    S_i = a.clk_s[i];
+                    c_rev = a.clk_c[i];
+                    g_rev = a.clk_g[i];
+                }
+                const double D = __dsub_rn(__dadd_rn(S_prev, (double)eps), S_i);
+                const double rhs = __dadd_rn(__dmul_rn(4.0, D), __dmul_rn(0x1p-20, __dadd_rn((double)g_rev, D)));
+                f[k] = ((double)c_rev <= rhs) ? 1u : 0u;
+            } else {
+                const float tau = __fmul_rn(0x1p-20f, __fadd_rn(__fadd_rn(d1, d2), eps));
+                float motion;           // the rule's bound on how much c can shrink, over 2
+                if (a.frontier_rule == CERT_FRONTIER_POINT) {
+                    // per-point budget: point i moved by delta_i (k_prepare keeps its square in w)
+                    motion = __fmul_rn(2.0f, __fadd_rn(__fsqrt_rn(a.pos_new[i].w), eps));
+                } else {
+                    motion = __fmul_rn(4.0f, eps);   // Algorithm 1, Lemma 1
+                }
+                f[k] = (c <= __fadd_rn(motion, tau)) ? 1u : 0u;
+            }
             a.inF[i] = (uint8_t)f[k];
         }
         sum += f[k];
@@ -1098,6 +1127,7 @@ __global__ void k_finalize(const StepArgs a)
         if (r.eps_t > __fmul_ru(a.declared_eps, 1.0f + 0x1p-20f)) atomicOr(a.status, ST_EBOUND);
         st.prev_fail_ratio = (float)acc.n_failed / (float)max(1, nF);
         st.prev_nfront = nF;
+        st.S = __dadd_rn(st.S, (double)r.eps_t);   // cumulative clock
     }
     st.g_cur = st.g_next;
     st.inv_g = __frcp_rn((float)st.g_cur);

@@ -31,6 +31,32 @@ the five the benchmark configurations name):
   seeded centre take eps-ball steps, the rest are static.
 * ``uniform_clusters``   half uniform, half in 16 Gaussian clusters
   (sigma 0.01); every point takes eps-ball steps (the large-N scale scene).
+
+The paper's other motion families (Sec. 3, Table 1) are named there but not
+parameterised; these are the build's own readings of them:
+
+* ``grid_jitter``        the first n sites, in seeded random order, of the
+  k^d lattice with spacing 1/k (k = ceil(n^(1/d))), cell-centred; eps-ball
+  steps from there (jittered-lattice diffusion; the exact lattice of the
+  first frame is full of equal distances).
+* ``filament``           points along the closed Lissajous curve
+  (0.5+0.35 sin 2 pi u, 0.5+0.35 sin 4 pi u[, 0.5+0.2 cos 2 pi u]) in a
+  Gaussian tube (sigma 0.01, clipped at 4.5 sigma), flowing along it at
+  <= 0.5 eps per step plus an accumulated 0.5 eps jitter.
+* ``vortex``             points uniform in the disk (cylinder in 3-D,
+  z in [0.1, 0.9]) of radius 0.4 about the centre, rotating differentially
+  with speed 0.5 eps * 4 (r/R)(1 - r/R) (zero at the axis and at the rim)
+  plus an accumulated 0.5 eps jitter.
+* ``split_merge``        one Gaussian cluster (sigma 0.05) whose two halves
+  move apart along +-x at 0.5 eps per step for half the horizon and back
+  for the other half, plus an accumulated 0.5 eps jitter.
+* ``shear_band``         uniform points; those in the band |y - 0.5| < 0.1
+  move along +x with speed eps * (1 - |y - 0.5| / 0.1), the rest are static.
+* ``spiral``             points at equal arc-length spacing on an
+  Archimedean spiral (r from 0.05 to 0.4 over 6 turns; in 3-D rising
+  linearly from z = 0.1 to 0.9), a near-lattice arrangement whose neighbours
+  along the arm are nearly equidistant, rotating rigidly by <= 0.5 eps per
+  step plus an accumulated 0.1 eps jitter.
 """
 from __future__ import annotations
 
@@ -41,7 +67,8 @@ import numpy as np
 
 FAMILIES = ("uniform_brownian", "clustered_drift", "ring_rotation",
             "adversarial_crossing", "hotspot")
-ALL_FAMILIES = FAMILIES + ("uniform_clusters",)
+PAPER_FAMILIES = ("grid_jitter", "filament", "vortex", "split_merge", "shear_band", "spiral")
+ALL_FAMILIES = FAMILIES + ("uniform_clusters",) + PAPER_FAMILIES
 _FAMILY_ID = {f: k for k, f in enumerate(ALL_FAMILIES)}
 STEP_FRACTION = 0.999
 
@@ -155,6 +182,104 @@ class Motion:
         x[nu:] = centres[lab] + 0.01 * r.standard_normal((n - nu, d))
         self._x = reflect(x[r.permutation(n)])
 
+    def _init_grid_jitter(self):
+        r, n, d = self._rng, self.n, self.dim
+        k = int(math.ceil(n ** (1.0 / d) - 1e-9))
+        while k ** d < n:
+            k += 1
+        idx = r.permutation(k ** d)[:n]
+        sites = np.stack(np.unravel_index(idx, (k,) * d), axis=1).astype(np.float64)
+        self._x = (sites + 0.5) / k
+
+    _FIL_LMAX = 2.0 * math.pi * math.sqrt(0.35 ** 2 + 0.7 ** 2 + 0.2 ** 2)   # bound on |c'(u)|
+
+    def _filament_curve(self, u):
+        c = np.empty((u.shape[0], self.dim))
+        c[:, 0] = 0.5 + 0.35 * np.sin(2.0 * math.pi * u)
+        c[:, 1] = 0.5 + 0.35 * np.sin(4.0 * math.pi * u)
+        if self.dim == 3:
+            c[:, 2] = 0.5 + 0.2 * np.cos(2.0 * math.pi * u)
+        return c
+
+    def _init_filament(self):
+        r, n, d = self._rng, self.n, self.dim
+        a = self._aux
+        a["u"] = r.random(n)
+        a["off"] = np.clip(0.01 * r.standard_normal((n, d)), -0.045, 0.045)
+        a["du"] = 0.5 * STEP_FRACTION * self.eps / self._FIL_LMAX
+        a["J"] = np.zeros((n, d))
+        self._x = self._filament_curve(a["u"]) + a["off"]
+
+    def _init_vortex(self):
+        r, n, d = self._rng, self.n, self.dim
+        a = self._aux
+        rad = 0.4 * np.sqrt(r.random(n))
+        a["r"] = rad
+        a["th"] = 2.0 * math.pi * r.random(n)
+        a["z"] = 0.1 + 0.8 * r.random(n) if d == 3 else None
+        speed = 0.5 * STEP_FRACTION * self.eps * 4.0 * (rad / 0.4) * (1.0 - rad / 0.4)
+        a["dth"] = np.where(rad > 0.0, speed / np.maximum(rad, 1e-30), 0.0)   # arc <= speed
+        a["J"] = np.zeros((n, d))
+        self._x = self._vortex_pos()
+
+    def _vortex_pos(self):
+        a = self._aux
+        th = a["th"] + a["dth"] * self.t
+        x = np.empty((self.n, self.dim))
+        x[:, 0] = 0.5 + a["r"] * np.cos(th)
+        x[:, 1] = 0.5 + a["r"] * np.sin(th)
+        if self.dim == 3:
+            x[:, 2] = a["z"]
+        return x + a["J"]
+
+    def _init_split_merge(self):
+        r, n, d = self._rng, self.n, self.dim
+        a = self._aux
+        a["base"] = 0.5 + np.clip(0.05 * r.standard_normal((n, d)), -0.3, 0.3)
+        a["sgn"] = np.where(r.random(n) < 0.5, -1.0, 1.0)
+        a["J"] = np.zeros((n, d))
+        self._x = self._split_pos()
+
+    def _split_pos(self):
+        a = self._aux
+        half = max(1, self.steps // 2)
+        t = self.t % (2 * half)
+        tri = t if t <= half else 2 * half - t                    # steps of separation
+        x = a["base"].copy()
+        x[:, 0] += a["sgn"] * 0.5 * STEP_FRACTION * self.eps * tri
+        return x + a["J"]
+
+    def _init_shear_band(self):
+        r, n, d = self._rng, self.n, self.dim
+        self._x = r.random((n, d))
+        w = np.clip(1.0 - np.abs(self._x[:, 1] - 0.5) / 0.1, 0.0, 1.0)
+        self._aux["v"] = STEP_FRACTION * self.eps * w
+
+    def _init_spiral(self):
+        r, n, d = self._rng, self.n, self.dim
+        a = self._aux
+        turns, r0, r1 = 6.0, 0.05, 0.4
+        phi = np.linspace(0.0, 2.0 * math.pi * turns, 200001)
+        rad = r0 + (r1 - r0) * phi / phi[-1]
+        pts = np.stack([rad * np.cos(phi), rad * np.sin(phi)], 1)
+        if d == 3:
+            pts = np.concatenate([pts, (0.1 + 0.8 * phi / phi[-1])[:, None]], 1)
+        seg = np.linalg.norm(np.diff(pts, axis=0), axis=1)
+        arc = np.concatenate([[0.0], np.cumsum(seg)])
+        s_i = (np.arange(n) + 0.5) / n * arc[-1]                   # equal arc-length spacing
+        ph = np.interp(s_i, arc, phi)
+        rr = r0 + (r1 - r0) * ph / phi[-1]
+        base = np.zeros((n, d))
+        base[:, 0] = rr * np.cos(ph)
+        base[:, 1] = rr * np.sin(ph)
+        if d == 3:
+            base[:, 2] = 0.1 + 0.8 * ph / phi[-1] - 0.5
+        perm = r.permutation(n)
+        a["base"] = base[perm]
+        a["omega"] = 0.5 * STEP_FRACTION * self.eps / r1     # arc per step <= 0.5 eps
+        a["J"] = np.zeros((n, d))
+        self._x = 0.5 + a["base"]
+
     # -- steps ---------------------------------------------------------------
     def _ball(self, frac: float, n: int | None = None) -> np.ndarray:
         return ball(self._rng, self.n if n is None else n, self.dim, frac * STEP_FRACTION * self.eps)
@@ -187,6 +312,38 @@ class Motion:
         k = int(hot.sum())
         if k:
             self._x[hot] = self._x[hot] + self._ball(1.0, k)
+
+    _step_grid_jitter = _step_uniform_brownian
+
+    def _step_filament(self):
+        a = self._aux
+        a["u"] = a["u"] + a["du"]
+        a["J"] = a["J"] + self._ball(0.5)
+        self._x = self._filament_curve(a["u"]) + a["off"] + a["J"]
+
+    def _step_vortex(self):
+        self._aux["J"] = self._aux["J"] + self._ball(0.5)
+        self._x = self._vortex_pos()
+
+    def _step_split_merge(self):
+        self._aux["J"] = self._aux["J"] + self._ball(0.5)
+        self._x = self._split_pos()
+
+    def _step_shear_band(self):
+        self._x = self._x.copy()
+        self._x[:, 0] = self._x[:, 0] + self._aux["v"]
+
+    def _step_spiral(self):
+        a = self._aux
+        th = a["omega"] * self.t
+        c, s = math.cos(th), math.sin(th)
+        b = a["base"]
+        y = b.copy()
+        y[:, 0] = c * b[:, 0] - s * b[:, 1]
+        y[:, 1] = s * b[:, 0] + c * b[:, 1]
+        if self.jitter:
+            a["J"] = a["J"] + self._ball(0.1)
+        self._x = 0.5 + y + a["J"]
 
     def frame(self) -> np.ndarray:
         return reflect(self._x).astype(np.float32)

@@ -66,9 +66,13 @@ def test_host_argument_validation_without_gpu(L):
     cfg.n_total = 2
     assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
     cfg.n_total = 10
-    cfg.reserved[0] = 1
+    cfg.reserved = 1
     assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
-    cfg.reserved[0] = 0
+    cfg.reserved = 0
+    cfg.frontier_rule = 3
+    assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
+    assert b"frontier_rule" in L.cert_last_error(None)
+    cfg.frontier_rule = 0
     cfg.bucket_factor = 3
     assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
     cfg.bucket_factor = 0

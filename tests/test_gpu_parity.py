@@ -152,6 +152,48 @@ def test_families_d3_rebuild_and_d2(torch, family):
     run_loop(torch, scenes.Motion(family, 3000, 2, 2e-3, seed=5, steps=6), 6, "incremental")
 
 
+@pytest.mark.parametrize("family", scenes.PAPER_FAMILIES)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_paper_families_incremental_and_rebuild(torch, family, dim):
+    """The paper's other motion families (Sec. 3, Table 1), both strategies."""
+    run_loop(torch, scenes.Motion(family, 3000, dim, 2e-3, seed=12, steps=10), 8, "incremental")
+    run_loop(torch, scenes.Motion(family, 2000, dim, 2e-3, seed=13, steps=10), 4, "rebuild")
+
+
+@pytest.mark.parametrize("rule", ["point", "clock"])
+@pytest.mark.parametrize("family", ["uniform_brownian", "hotspot", "adversarial_crossing", "vortex", "grid_jitter"])
+def test_frontier_rules_match_oracle(torch, rule, family):
+    """The per-point budget and cumulative-clock frontier rules: the detected
+    frontier, its cells and H_cand bit-exact / within 1e-6 of the oracle over a
+    dozen steps (the clock carries state across them), certificates unchanged."""
+    from paper_2606_18314_b300 import cert
+    for dim, strategy in ((3, "incremental"), (2, "rebuild")):
+        m = scenes.Motion(family, 2500, dim, 2e-3, seed=14, steps=30)
+        p = m.frame()
+        ctx = cert.Context(dev(torch, p), frontier_rule=rule)
+        ref = oracle.top2(p)
+        clock = oracle.ClockState(ref) if rule == "clock" else None
+        for t in range(12):
+            q = m.advance()
+            ctx.step(dev(torch, q), 2e-3, strategy)
+            res, _ = ctx.sync()
+            r = oracle.step(p, q, ref, rule=rule, clock=clock)
+            assert_step_equal(ctx, res, ctx.views(), r, tag=f"{rule} {family} d={dim} step {t}")
+            p, ref = q, r.cert
+        if rule == "clock":
+            # a rebuild revisits every point; the clock keeps running
+            ctx.rebuild()
+            clock._revisit(ref, np.ones(ref.nn.shape[0], bool))
+            for t in range(3):
+                q = m.advance()
+                ctx.step(dev(torch, q), 2e-3, strategy)
+                res, _ = ctx.sync()
+                r = oracle.step(p, q, ref, rule=rule, clock=clock)
+                assert_step_equal(ctx, res, ctx.views(), r, tag=f"clock after rebuild {family} step {t}")
+                p, ref = q, r.cert
+        ctx.close()
+
+
 def test_strategies_agree_bitwise(torch):
     from paper_2606_18314_b300 import cert
     m = scenes.BatchMotion.mixed(n_scenes=5, lo=800, hi=3000, eps=2e-3, seed=7)

@@ -291,7 +291,7 @@ def test_trunc_median(oracle_mod):
 
 # --------------------------------------------------------------------------- full step / audit
 
-@pytest.mark.parametrize("family", scenes.FAMILIES)
+@pytest.mark.parametrize("family", scenes.ALL_FAMILIES)
 @pytest.mark.parametrize("dim", [2, 3])
 def test_safety_rule_never_misses(oracle_mod, family, dim):
     """Lemma 1 / Cor. A.2 / Table 1 'miss (safe) = 0' on every family."""

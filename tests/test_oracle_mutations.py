@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_core as pins
+from tests import test_oracle_frontier_rules as rules
 
 MUTANTS = {
     "drop_dz": ("s = s + dz * dz;", "s = s;"),
@@ -19,6 +20,8 @@ MUTANTS = {
     "cells_transposed": ("(k[2] * g + k[1]) * g + k[0]", "(k[0] * g + k[1]) * g + k[2]"),
     "entropy_norm_m": ("H = s / log((double)C);", "H = s / log((double)m);"),
     "eps_first_point": ("if (D > m)\n            m = D;", "if (i == 0)\n            m = D;"),
+    "point_budget_halved": ("float rhs = 2.0f * (disp[i] + eps) + tau;", "float rhs = (disp[i] + eps) + tau;"),
+    "point_budget_own_only": ("float rhs = 2.0f * (disp[i] + eps) + tau;", "float rhs = 2.0f * disp[i] + tau;"),
 }
 
 PIN_CALLS = [
@@ -31,6 +34,9 @@ PIN_CALLS = [
     lambda o: pins.test_cells_dyadic_and_clamped(o),
     lambda o: pins.test_entropy_closed_forms(o),
     lambda o: pins.test_eps_is_max_displacement(o),
+    lambda o: rules.test_point_and_clock_rules_never_miss("adversarial_crossing", 3),
+    lambda o: rules.test_point_and_clock_rules_never_miss("clustered_drift", 2),
+    lambda o: rules.test_point_rule_leaves_out_a_static_point_with_clearance_three_eps(),
 ]
 
 
