@@ -12,6 +12,8 @@
 // gives a deterministic result independent of how the j-range was split.
 // The work is plain FP32 arithmetic (no tensor cores: the inner dimension is
 // d <= 3 and the fixed rounding order forbids the |x|^2 + |y|^2 - 2xy form).
+#include <algorithm>
+
 #include "cert_internal.cuh"
 #include "cert_launch.h"
 
@@ -61,6 +63,25 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One staged tile against this thread's kApQ queries (packed in pairs).
+template <int DIM, bool CHECK_SELF>
+__device__ __forceinline__ void visit_tile(const float4 *s_tile, int len, int jb, const unsigned long long *qx,
+                                           const unsigned long long *qy, const unsigned long long *qz,
+                                           const int *qi, Top3 *t)
+{
+    for (int jj = 0; jj < len; ++jj) {
+        const float4 c = s_tile[jj];
+        const int j = jb + jj;
+#pragma unroll
+        for (int k = 0; k < kApQ; k += 2) {
+            float D0, D1;
+            sqdist_qpair<DIM>(qx[k / 2], qy[k / 2], qz[k / 2], c, D0, D1);
+            if (D0 < t[k].d2 && (!CHECK_SELF || j != qi[k])) top3_insert(t[k], D0, j);
+            if (D1 < t[k + 1].d2 && (!CHECK_SELF || j != qi[k + 1])) top3_insert(t[k + 1], D1, j);
+        }
+    }
 }
 
 template <int DIM>
@@ -125,17 +146,15 @@ __global__ void __launch_bounds__(kApThreads) k_allpairs(const APArgs a)
         if (__syncthreads_or(!ready)) break;
         phase ^= 1u;
         const int jb = sp.pt_off + jt;
-        for (int jj = 0; jj < len; ++jj) {
-            const float4 c = s_tile[jj];
-            const int j = jb + jj;
-#pragma unroll
-            for (int k = 0; k < kApQ; k += 2) {
-                float D0, D1;
-                sqdist_qpair<DIM>(qx[k / 2], qy[k / 2], qz[k / 2], c, D0, D1);
-                if (D0 < t[k].d2 && j != qi[k]) top3_insert(t[k], D0, j);
-                if (D1 < t[k + 1].d2 && j != qi[k + 1]) top3_insert(t[k + 1], D1, j);
-            }
-        }
+        // a tile can hold one of this CTA's own queries only where the index
+        // ranges meet (always possible for a query list); elsewhere the
+        // self-exclusion test is dropped from the inner loop
+        const int qlo = it.qb * kApQBlock;
+        const bool own = a.queries != nullptr || (jt < qlo + kApQBlock && jt + len > qlo);
+        if (own)
+            visit_tile<DIM, true>(s_tile, len, jb, qx, qy, qz, qi, t);
+        else
+            visit_tile<DIM, false>(s_tile, len, jb, qx, qy, qz, qi, t);
         __syncthreads();
     }
 
@@ -244,6 +263,35 @@ __global__ void k_pack(const float *pos, int n, float4 *out, uint32_t *status)
     const float4 p = make_float4(q[0], q[1], DIM == 3 ? q[2] : 0.0f, 0.0f);
     if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) atomicOr(status, ST_NONFINITE);
     out[i] = p;
+}
+
+int allpairs_chunks(long long qblocks, int dim, int cap)
+{
+    // j-chunks per query block so that the grid fills whole waves of resident
+    // CTAs: the smallest count giving at least one full wave at >= 90% of the
+    // last wave, else the best fill found
+    int dev = 0, sms = 1, bps = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        sms = 148;
+    const cudaError_t e = (dim == 3) ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_allpairs<3>, kApThreads, 0)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_allpairs<2>, kApThreads, 0);
+    if (e != cudaSuccess || bps < 1) bps = 1;
+    const long long wave = (long long)sms * bps;
+    cap = std::max(1, std::min(cap, 64));
+    int best = 1;
+    double best_fill = -1.0;
+    for (int nch = 1; nch <= cap; ++nch) {
+        const long long ctas = qblocks * nch;
+        const long long waves = (ctas + wave - 1) / wave;
+        const double fill = (double)ctas / (double)(waves * wave);
+        if (ctas >= wave && fill >= 0.9) return nch;
+        if (fill > best_fill + 1e-9) {
+            best_fill = fill;
+            best = nch;
+        }
+    }
+    return best;
 }
 
 cudaError_t launch_allpairs(const APArgs &a, cudaStream_t st)

@@ -82,10 +82,13 @@ extern "C" cert_status cert_allpairs_noalloc(const float *d_pos, int64_t n, int3
     if (nq < 0 || nq >= (int64_t(1) << 30)) return noalloc_fail(CERT_EINVAL, "bad query count");
     if (nq == 0) return CERT_OK;
 
-    // Same decomposition as cert_allpairs: 512 queries per CTA, enough j-chunks
-    // to give about 8 CTAs per SM.
+    // Same decomposition as cert_allpairs (512 queries per CTA, j-chunks filling
+    // whole waves), with the chunk count also capped by the scratch it needs.
     const int64_t nqb = (nq + kApQBlock - 1) / kApQBlock;
-    const int64_t nch = std::max<int64_t>(1, std::min<int64_t>((148 * 8 + nqb - 1) / nqb, (n + 255) / 256));
+    const int64_t room = (int64_t)kNoAllocScratchBytes - (int64_t)align256(size_t(n) * sizeof(float4)) - 4096;
+    const int64_t fit = room > 0 ? room / (nq * int64_t(6 * sizeof(float))) : 1;
+    const int64_t nch = allpairs_chunks(nqb, dim, (int)std::max<int64_t>(
+                                                      1, std::min<int64_t>({fit, (n + 255) / 256, int64_t(64)})));
     const long long P = (long long)nq * nch;
     const size_t o_pos = 0;
     const size_t o_sp = align256(o_pos + size_t(n) * sizeof(float4));

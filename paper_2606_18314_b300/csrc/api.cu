@@ -271,7 +271,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->h_sp.resize(c->S);
     int64_t boff = 0, hoff = 0, apoff = 0, total_qb = 0, quads = 0;
     for (int k = 0; k < c->S; ++k) total_qb += ceil_div(off[k + 1] - off[k], kApQBlock);
-    const int64_t nch_all = std::min<int64_t>(64, std::max<int64_t>(1, ceil_div(148 * 8, total_qb)));
+    const int64_t nch_all = allpairs_chunks(total_qb, c->dim, 64);
     std::vector<APItem> items;
     for (int k = 0; k < c->S; ++k) {
         SceneParams &p = c->h_sp[k];
@@ -857,7 +857,7 @@ extern "C" cert_status cert_allpairs(const float *d_pos, int64_t n, int32_t dim,
     if (nq == 0) return CERT_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int nqb = (int)ceil_div(nq, kApQBlock);
-    const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(148 * 8, nqb), ceil_div(n, 256)));
+    const int nch = allpairs_chunks(nqb, dim, (int)std::min<int64_t>(64, ceil_div(n, 256)));
     SceneParams p;
     std::memset(&p, 0, sizeof(p));
     p.pt_off = 0;

@@ -103,6 +103,8 @@ constexpr int kApQBlock = kApThreads * kApQ;   // queries per block
 constexpr int kApTile = 2048;                  // candidates staged per shared-memory tile
 
 cudaError_t launch_allpairs(const APArgs &a, cudaStream_t st);
+// j-chunks per query block that fill whole waves of resident k_allpairs CTAs (1 <= result <= cap).
+int allpairs_chunks(long long qblocks, int dim, int cap);
 cudaError_t launch_allpairs_merge(const APArgs &a, const APMergeOut &o, long long n_queries_total,
                                   cudaStream_t st);
 cudaError_t launch_pack(const float *pos, int n, int dim, float4 *out, uint32_t *status, cudaStream_t st);

@@ -41,10 +41,23 @@ def test_noalloc_matches_allpairs_on_consecutive_calls():
         assert np.array_equal(got[2].cpu().numpy().view(np.uint32), o.d2sq.view(np.uint32))
 
 
+def test_noalloc_at_its_documented_limit():
+    """n = nq = 838,000 (the documented limit) fits and equals cert_allpairs."""
+    import torch
+    from paper_2606_18314_b300 import cert
+    n = 838_000
+    p = torch.rand((n, 3), generator=torch.Generator().manual_seed(7)).cuda()
+    ref = cert.cert_allpairs(p)
+    got = cert.cert_allpairs_noalloc(p)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, got):
+        assert torch.equal(a, b)
+
+
 def test_noalloc_rejects_sizes_beyond_its_array():
     import torch
     from paper_2606_18314_b300 import cert
-    n = 560_000                       # needs more than the 32 MiB scratch array
+    n = 900_000                       # needs more than the 32 MiB scratch array
     p = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
     with pytest.raises(cert.CertError) as ei:
         cert.cert_allpairs_noalloc(p)
