@@ -65,21 +65,62 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// One staged tile against this thread's kApQ queries (packed in pairs).
-template <int DIM, bool CHECK_SELF>
-__device__ __forceinline__ void visit_tile(const float4 *s_tile, int len, int jb, const unsigned long long *qx,
-                                           const unsigned long long *qy, const unsigned long long *qz,
-                                           const int *qi, Top3 *t)
+// Candidates staged per TMA copy; the staged tile is rewritten as candidate
+// pairs (xa, xb, ya, yb) and (za, zb), so that one 16-byte and one 8-byte
+// shared load give each coordinate of two candidates as one f32x2 operand.
+constexpr int kApStage = 1024;
+
+// Squared distances of two candidates (coordinates packed pairwise: cx =
+// {xa, xb}, ...) to the query whose coordinates are packed twice (px = {x,
+// x}, ...): packed differences and squares, scalar additions -- bit-identical
+// to sqdist<DIM>(query, candidate) for each candidate.
+template <int DIM>
+__device__ __forceinline__ void sqdist_cpair(unsigned long long px, unsigned long long py, unsigned long long pz,
+                                             unsigned long long cx, unsigned long long cy, unsigned long long cz,
+                                             float &Da, float &Db)
 {
-    for (int jj = 0; jj < len; ++jj) {
-        const float4 c = s_tile[jj];
-        const int j = jb + jj;
+    unsigned long long dx, dy;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(cx), "l"(px));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(cy), "l"(py));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(dx) : "l"(dx));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(dy) : "l"(dy));
+    float xa, xb, ya, yb;
+    unpack2(dx, xa, xb);
+    unpack2(dy, ya, yb);
+    Da = __fadd_rn(xa, ya);
+    Db = __fadd_rn(xb, yb);
+    if (DIM == 3) {
+        unsigned long long dz;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(cz), "l"(pz));
+        asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(dz) : "l"(dz));
+        float za, zb;
+        unpack2(dz, za, zb);
+        Da = __fadd_rn(Da, za);
+        Db = __fadd_rn(Db, zb);
+    }
+}
+
+// One converted tile (npair candidate pairs, the first with index jb) against
+// this thread's kApQ queries.  Candidates are visited in ascending index, so
+// the strict '<' keeps the lowest index among equal distances.
+template <int DIM, bool CHECK_SELF>
+__device__ __forceinline__ void visit_pairs(const float4 *s_xy, const float2 *s_z, int npair, int jb,
+                                            const unsigned long long *px, const unsigned long long *py,
+                                            const unsigned long long *pz, const int *qi, Top3 *t)
+{
+    for (int pp = 0; pp < npair; ++pp) {
+        const float4 xy = s_xy[pp];
+        const float2 zz = (DIM == 3) ? s_z[pp] : make_float2(0.f, 0.f);
+        const unsigned long long cx = pack2(xy.x, xy.y), cy = pack2(xy.z, xy.w), cz = pack2(zz.x, zz.y);
+        const int ja = jb + 2 * pp, jn = ja + 1;
 #pragma unroll
-        for (int k = 0; k < kApQ; k += 2) {
-            float D0, D1;
-            sqdist_qpair<DIM>(qx[k / 2], qy[k / 2], qz[k / 2], c, D0, D1);
-            if (D0 < t[k].d2 && (!CHECK_SELF || j != qi[k])) top3_insert(t[k], D0, j);
-            if (D1 < t[k + 1].d2 && (!CHECK_SELF || j != qi[k + 1])) top3_insert(t[k + 1], D1, j);
+        for (int k = 0; k < kApQ; ++k) {
+            float Da, Db;
+            sqdist_cpair<DIM>(px[k], py[k], pz[k], cx, cy, cz, Da, Db);
+            if (fminf(Da, Db) < t[k].d2) {
+                if (Da < t[k].d2 && (!CHECK_SELF || ja != qi[k])) top3_insert(t[k], Da, ja);
+                if (Db < t[k].d2 && (!CHECK_SELF || jn != qi[k])) top3_insert(t[k], Db, jn);
+            }
         }
     }
 }
@@ -87,7 +128,9 @@ __device__ __forceinline__ void visit_tile(const float4 *s_tile, int len, int jb
 template <int DIM>
 __global__ void __launch_bounds__(kApThreads) k_allpairs(const APArgs a)
 {
-    __shared__ __align__(128) float4 s_tile[kApTile];
+    __shared__ __align__(128) float4 s_tile[kApStage];        // TMA staging (x, y, z, w) per candidate
+    __shared__ __align__(16) float4 s_xy[kApStage / 2];       // (xa, xb, ya, yb) per candidate pair
+    __shared__ __align__(16) float2 s_z[kApStage / 2];        // (za, zb)
     __shared__ __align__(8) uint64_t s_bar;
 
     APItem it;
@@ -120,24 +163,28 @@ __global__ void __launch_bounds__(kApThreads) k_allpairs(const APArgs a)
     }
     __syncthreads();
 
-    // queries packed pairwise for the f32x2 arithmetic
-    unsigned long long qx[kApQ / 2], qy[kApQ / 2], qz[kApQ / 2];
+    // each query's coordinates packed twice for the f32x2 arithmetic
+    unsigned long long px[kApQ], py[kApQ], pz[kApQ];
 #pragma unroll
-    for (int k = 0; k < kApQ / 2; ++k) {
-        qx[k] = pack2(qp[2 * k].x, qp[2 * k + 1].x);
-        qy[k] = pack2(qp[2 * k].y, qp[2 * k + 1].y);
-        qz[k] = pack2(qp[2 * k].z, qp[2 * k + 1].z);
+    for (int k = 0; k < kApQ; ++k) {
+        px[k] = pack2(qp[k].x, qp[k].x);
+        py[k] = pack2(qp[k].y, qp[k].y);
+        pz[k] = pack2(qp[k].z, qp[k].z);
     }
     const int j0 = it.chunk * sp.ap_chunk;
     const int j1 = min(sp.n, j0 + sp.ap_chunk);
+    const int qlo = it.qb * kApQBlock;
     uint32_t phase = 0;
-    for (int jt = j0; jt < j1; jt += kApTile) {
-        const int len = min(kApTile, j1 - jt);
-        if (threadIdx.x == 0) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&s_bar, (uint32_t)len * 16u);
-            bulk_copy_g2s(s_tile, a.pos + sp.pt_off + jt, (uint32_t)len * 16u, &s_bar);
-        }
+    // the first tile's copy; each later one is issued once the previous tile
+    // has been converted, so it overlaps the distance work
+    if (threadIdx.x == 0 && j0 < j1) {
+        const int len = min(kApStage, j1 - j0);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar, (uint32_t)len * 16u);
+        bulk_copy_g2s(s_tile, a.pos + sp.pt_off + j0, (uint32_t)len * 16u, &s_bar);
+    }
+    for (int jt = j0; jt < j1; jt += kApStage) {
+        const int len = min(kApStage, j1 - jt);
         uint32_t spins = 0;
         bool ready;
         while (!(ready = mbar_try_wait(&s_bar, phase)))
@@ -145,16 +192,32 @@ __global__ void __launch_bounds__(kApThreads) k_allpairs(const APArgs a)
         if (!ready) atomicOr(a.status, ST_TIMEOUT);
         if (__syncthreads_or(!ready)) break;
         phase ^= 1u;
+        // staged candidates -> pairs; an odd tail is paired with a NaN candidate
+        const int npair = (len + 1) >> 1;
+        for (int pp = threadIdx.x; pp < npair; pp += kApThreads) {
+            const float4 ca = s_tile[2 * pp];
+            const float4 cb = (2 * pp + 1 < len) ? s_tile[2 * pp + 1]
+                                                 : make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
+                                                               __int_as_float(0x7fc00000), 0.f);
+            s_xy[pp] = make_float4(ca.x, cb.x, ca.y, cb.y);
+            s_z[pp] = make_float2(ca.z, cb.z);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && jt + kApStage < j1) {
+            const int ln = min(kApStage, j1 - jt - kApStage);
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&s_bar, (uint32_t)ln * 16u);
+            bulk_copy_g2s(s_tile, a.pos + sp.pt_off + jt + kApStage, (uint32_t)ln * 16u, &s_bar);
+        }
         const int jb = sp.pt_off + jt;
         // a tile can hold one of this CTA's own queries only where the index
         // ranges meet (always possible for a query list); elsewhere the
         // self-exclusion test is dropped from the inner loop
-        const int qlo = it.qb * kApQBlock;
         const bool own = a.queries != nullptr || (jt < qlo + kApQBlock && jt + len > qlo);
         if (own)
-            visit_tile<DIM, true>(s_tile, len, jb, qx, qy, qz, qi, t);
+            visit_pairs<DIM, true>(s_xy, s_z, npair, jb, px, py, pz, qi, t);
         else
-            visit_tile<DIM, false>(s_tile, len, jb, qx, qy, qz, qi, t);
+            visit_pairs<DIM, false>(s_xy, s_z, npair, jb, px, py, pz, qi, t);
         __syncthreads();
     }
 
