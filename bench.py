@@ -515,9 +515,23 @@ def main():
     el = time.perf_counter() - t0
     clock[0] += E
     assert int(out["n_missed"].sum()) == 0, "safety rule missed a failure"
+    # the host link alone: one frame's pinned host-to-device copy, CUDA events
+    stage = torch.empty((N, dim), dtype=torch.float32, device="cuda")
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        stage.copy_(host_frames[0], non_blocking=True)
+    h0.record(stream)
+    for _ in range(5):
+        stage.copy_(host_frames[0], non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    h2d_ms = h0.elapsed_time(h1) / 5
+    del stage
     e2e = {"value": N * E / el * (n_all / N), "unit": UNIT, "h2d_bytes_per_step": row_bytes,
            "d2h_bytes_per_step": int(S * cert.SCENE_DTYPE.itemsize), "steps": E,
-           "api": "cert_step_host_stream (copies pipelined against the steps)"}
+           "api": "cert_step_host_stream (copies pipelined against the steps)",
+           "h2d_ms_per_frame": h2d_ms, "h2d_gbs": row_bytes / (h2d_ms * 1e-3) / 1e9,
+           "link_bound": N / (h2d_ms * 1e-3) * (n_all / N)}
 
     # ---- the all-pairs pass (exact brute force) at the paper's Table 2 sizes
     allpairs = None
