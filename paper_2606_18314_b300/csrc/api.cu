@@ -63,6 +63,17 @@ struct cert_ctx {
     // pipelined host steps: a second staging buffer, a copy stream and events (created on first use)
     float *stage2 = nullptr;
     cudaStream_t copy_stream = nullptr;
+    // one-step CUDA graphs replayed by the pipelined host steps, one per
+    // (position buffer, staging buffer) parity; rebuilt when eps, the strategy
+    // or a setting baked into the step arguments changes
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        float eps = 0.0f;
+        int strategy = -1;
+        uint64_t epoch = 0;
+    } step_graph[4];
+    cudaStream_t capture_stream = nullptr;
+    uint64_t settings_epoch = 1;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
     size_t snap_bytes = 0;
     int snap_cur = 0;
@@ -515,6 +526,47 @@ cert_status cert_step_host(cert_ctx *c, const float *h_pos_new, float eps, int32
     return CERT_OK;
 }
 
+// One step on `stream` by replaying a captured graph of cert_step for this
+// parity of the position and staging buffers (captured on first use).
+static cert_status step_by_graph(cert_ctx *c, const float *stage, int b, float eps, int32_t strategy,
+                                 cudaStream_t s)
+{
+    cert_ctx::StepGraph &g = c->step_graph[c->cur * 2 + b];
+    if (!g.exec || g.eps != eps || g.strategy != strategy || g.epoch != c->settings_epoch) {
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        if (!c->capture_stream) CK(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+        const int cur0 = c->cur;
+        const cudaStream_t last0 = c->last;
+        const bool stepped0 = c->stepped;
+        CK(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+        const cert_status rc = cert_step(c, stage, eps, strategy, nullptr, c->capture_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->capture_stream, &graph);
+        c->cur = cur0;              // the capture enqueued nothing: undo its bookkeeping
+        c->last = last0;
+        c->stepped = stepped0;
+        if (rc != CERT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        CK(c, e);
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(c, ei);
+        g.eps = eps;
+        g.strategy = strategy;
+        g.epoch = c->settings_epoch;
+    }
+    CK(c, cudaGraphLaunch(g.exec, s));
+    c->cur ^= 1;
+    c->last = s;
+    c->stepped = true;
+    return CERT_OK;
+}
+
 cert_status cert_step_host_stream(cert_ctx *c, const float *const *h_frames, int32_t n_steps, float eps,
                                   int32_t strategy, cert_scene_result *h_scenes, void *stream)
 {
@@ -543,7 +595,9 @@ cert_status cert_step_host_stream(cert_ctx *c, const float *const *h_frames, int
                               cudaMemcpyHostToDevice, c->copy_stream));
         CK(c, cudaEventRecord(c->ev_copied[b], c->copy_stream));
         CK(c, cudaStreamWaitEvent(s, c->ev_copied[b], 0));
-        const cert_status rc = cert_step(c, buf[b], eps, strategy, nullptr, stream);
+        // replayed as a graph (fewer launch gaps) unless phase profiling is on
+        const cert_status rc = c->prof_on ? cert_step(c, buf[b], eps, strategy, nullptr, stream)
+                                          : step_by_graph(c, buf[b], b, eps, strategy, s);
         if (rc != CERT_OK) return rc;
         CK(c, cudaEventRecord(c->ev_used[b], s));
         if (h_scenes)
@@ -637,6 +691,7 @@ cert_status cert_set_cell_scale(cert_ctx *c, float scale)
     if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
     if (!(scale > 0.0f) || !std::isfinite(scale)) return fail(c, CERT_EINVAL, "cell_scale must be finite and > 0");
     c->cell_scale = scale;
+    ++c->settings_epoch;
     return CERT_OK;
 }
 
@@ -647,6 +702,7 @@ cert_status cert_set_cell_quantile(cert_ctx *c, float q)
     if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
     if (!(q > 0.0f && q <= 1.0f)) return fail(c, CERT_EINVAL, "cell_quantile must be in (0, 1]");
     c->cell_quantile = q;
+    ++c->settings_epoch;
     return CERT_OK;
 }
 
@@ -664,6 +720,7 @@ cert_status cert_selector_load(cert_ctx *c, const float *h_params, const float *
     CK(c, cudaStreamSynchronize(c->last));
     if (!h_params) {
         c->have_sel = false;
+        ++c->settings_epoch;
         return CERT_OK;
     }
     if (!h_norm) return fail(c, CERT_EINVAL, "feature normalisation is NULL");
@@ -674,6 +731,7 @@ cert_status cert_selector_load(cert_ctx *c, const float *h_params, const float *
     CK(c, cudaMemcpy(c->sel_params, h_params, CERT_MLP_PARAMS * sizeof(float), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->sel_norm, h_norm, 16 * sizeof(float), cudaMemcpyHostToDevice));
     c->have_sel = true;
+    ++c->settings_epoch;
     return CERT_OK;
 }
 
@@ -771,6 +829,7 @@ cert_status cert_autotune(cert_ctx *c, const float *d_frames, int64_t frame_stri
     cudaEventDestroy(e1);
     cert_status rc2 = cert_restore(c, stream);
     c->cell_scale = (rc == CERT_OK) ? best : keep;
+    ++c->settings_epoch;
     if (h_best) *h_best = c->cell_scale;
     if (rc == CERT_OK) rc = rc2;
     // drop any status the probe steps latched (e.g. EBOUND from the caller's frames)
@@ -788,6 +847,9 @@ void cert_destroy(cert_ctx *c)
         if (c->ev_used[k]) cudaEventDestroy(c->ev_used[k]);
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (auto &g : c->step_graph)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     cudaFree(c->blob);
     delete c;

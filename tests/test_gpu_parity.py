@@ -383,5 +383,25 @@ def test_pipelined_host_steps_match_the_oracle(torch):
     for s in range(len(off) - 1):
         assert np.array_equal(host(v["nn"])[off[s]:off[s + 1]], prev[s].nn)
         assert np.array_equal(host(v["d2sq"])[off[s]:off[s + 1]].view(np.uint32), prev[s].d2sq.view(np.uint32))
+    # the steps replay captured graphs: a changed setting (cell scale) and a
+    # changed strategy must take effect in the next call, odd step counts too
+    ctx.set_cell_scale(2.0)
+    for order2, strat in (([3, 4, 3], cert.CERT_REBUILD), ([2], cert.CERT_INCREMENTAL)):
+        last = order[-1]
+        out2 = np.zeros(len(order2) * (len(off) - 1), cert.SCENE_DTYPE)
+        ctx.step_host_stream([host_frames.data_ptr() + k * row for k in order2], 2e-3, strat, out2)
+        for step, k in enumerate(order2):
+            src = last if step == 0 else order2[step - 1]
+            for s in range(len(off) - 1):
+                r = oracle.step(fr[src][off[s]:off[s + 1]], fr[k][off[s]:off[s + 1]], prev[s])
+                sc = out2[step * (len(off) - 1) + s]
+                assert int(sc["n_failed"]) == r.n_failed and int(sc["strategy"]) == strat, (order2, step, s)
+                prev[s] = r.cert
+        order = order + order2
+        v = ctx.views()
+        for s in range(len(off) - 1):
+            assert np.array_equal(host(v["nn"])[off[s]:off[s + 1]], prev[s].nn)
+            assert np.array_equal(host(v["d1sq"])[off[s]:off[s + 1]].view(np.uint32), prev[s].d1sq.view(np.uint32))
+        assert ctx.views() is not None
     with pytest.raises(cert.CertError):
         ctx.step_host_stream([0], 2e-3, cert.CERT_INCREMENTAL, None)
