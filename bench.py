@@ -302,6 +302,8 @@ def main():
     ap.add_argument("--prof-steps", type=int, default=200)
     ap.add_argument("--regret-steps", type=int, default=32)
     ap.add_argument("--rule-steps", type=int, default=32, help="steps per frontier rule in the detection report")
+    ap.add_argument("--matched-steps", type=int, default=48,
+                    help="transitions surveyed per scene in the matched-pair entropy experiment (0: skip)")
     ap.add_argument("--compare-steps", type=int, default=256)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -463,6 +465,14 @@ def main():
             assert tot[3] == 0, f"frontier rule {rule} missed a failure"
         rules["steps"] = args.rule_steps
 
+    # ---- the matched pair (Sec. 4, Fig. 2): equal failure counts, different
+    # entropy; the GPU repair timed on both (one scene of 16,000 points, and a
+    # batch of 64 seeds of each transition)
+    matched_pair = None
+    if args.matched_steps > 0 and rank == 0:
+        from paper_2606_18314_b300 import matched
+        matched_pair = matched.run(cert, steps=args.matched_steps)
+
     # ---- per-phase timing (CUDA events on the launching stream), same workload, eager
     P = max(1, args.prof_steps)
     ctx.profile_begin(P)
@@ -581,7 +591,7 @@ def main():
                 "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
                 "step_counts": step_counts, "compare": compare, "regret": regret, "frontier_rules": rules,
-                "allpairs": allpairs,
+                "matched_pair": matched_pair, "allpairs": allpairs,
                 "status": cert.STATUS_NAMES[rc] if 0 <= rc < len(cert.STATUS_NAMES) else rc}
         print(json.dumps(line), flush=True)
     ctx.close()
