@@ -452,17 +452,24 @@ def main():
     if args.rule_steps > 0:
         rules = {}
         for rule in ("step", "point", "clock"):
-            c3 = cert.Context(dev_frames[0], offsets=offsets, frontier_rule=rule, cell_scale=ctx.cell_scale())
-            tot = np.zeros(4)
+            c3 = cert.Context(dev_frames[0], offsets=offsets, frontier_rule=rule, cell_scale=ctx.cell_scale(),
+                              rho_audit=True)
+            tot = np.zeros(6)
             for k in range(1, args.rule_steps + 1):
                 c3.step(dev_frames[cycle_index(k, F)], eps, cert.CERT_INCREMENTAL)
                 r, _ = c3.sync(raise_on_status=False)
-                tot += [r["n_frontier"].sum(), r["n_failed"].sum(), r["n_false"].sum(), r["n_missed"].sum()]
+                tot += [r["n_frontier"].sum(), r["n_failed"].sum(), r["n_false"].sum(), r["n_missed"].sum(),
+                        r["n_rho"].sum(), r["n_rho_hit"].sum()]
             c3.close()
             rules[rule] = {"detected_frac": float(tot[0] / (N * args.rule_steps)),
                            "failed_frac": float(tot[1] / (N * args.rule_steps)),
                            "false_revalidation": float(tot[2] / max(1.0, tot[0])), "missed": int(tot[3])}
             assert tot[3] == 0, f"frontier rule {rule} missed a failure"
+        # the local heuristic rho_i = delta_i / c_i > 1/2 (Sec. 3, Table 1): the
+        # same on every rule's pass (it reads the same certificates and motion)
+        rules["rho"] = {"flagged_frac": float(tot[4] / (N * args.rule_steps)),
+                        "recall": float(tot[5] / max(1.0, tot[1])),
+                        "false": float((tot[4] - tot[5]) / max(1.0, tot[4]))}
         rules["steps"] = args.rule_steps
 
     # ---- the matched pair (Sec. 4, Fig. 2): equal failure counts, different

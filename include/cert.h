@@ -98,7 +98,9 @@ typedef struct {
     float cell_quantile;      /* reference d2 = this quantile of a scene's previous d2
                                  over its first min(n,1024) points, in (0,1] (0 -> 0.5) */
     int32_t frontier_rule;    /* cert_frontier_rule (0 -> CERT_FRONTIER_STEP)          */
-    int32_t reserved;         /* must be zero                                          */
+    int32_t rho_audit;        /* 1: count the local heuristic rho_i = delta_i / c_i > 1/2
+                                 of Sec. 3 each step (n_rho, n_rho_hit); 0: off, both
+                                 counts 0.  Other values are rejected.                   */
 } cert_config;
 
 /* Per-scene scalars of the last step.  Same layout on device and host. */
@@ -122,6 +124,11 @@ typedef struct {
     float pred_reb;           /* selector output: predicted ln step time, rebuild               */
     int32_t grid_res;         /* entropy-grid cells per axis (smallest g with g^dim >= n)      */
     int32_t search_res;       /* search-grid cells per axis used this step                      */
+    int32_t n_rho;            /* with rho_audit: #{i : 2 delta_i > c_i}, delta_i = |p'_i - p_i|
+                                 and c_i the pre-step clearance, both FP32 (the heuristic
+                                 rho_i > 1/2 of Sec. 3 and Table 1; a guess, not a bound)     */
+    int32_t n_rho_hit;        /* with rho_audit: flagged points whose nn changed; recall =
+                                 n_rho_hit / n_failed, false = (n_rho - n_rho_hit) / n_rho      */
 } cert_scene_result;
 
 /* Device views of the per-point results; valid until the next call that

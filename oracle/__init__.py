@@ -15,6 +15,8 @@ Nearest-Neighbour Structures"):
   Algorithm 1 (second statement), Lemma 1.
 * ``frontier_point`` -- the per-point motion budget c_i <= 2 (delta_i + eps)
   (+ guard), the remark closing Sec. 5; ``disp`` gives delta_i.
+* ``rho`` -- the local heuristic rho_i = delta_i / c_i > 1/2 of Sec. 3 and
+  Table 1 (recall and false-flag audit; not a bound).
 * ``ClockState`` -- the cumulative clock of the per-step cost subsection
   (Thm A.3): a certificate last revisited at clock S_i with clearance c^rev_i
   stays valid while 4 (S - S_i) < c^rev_i.
@@ -75,6 +77,8 @@ def lib():
         L.oracle_disp.restype = None
         L.oracle_frontier_point.argtypes = [f32p, f32p, f32p, ctypes.c_int64, ctypes.c_float, i32p]
         L.oracle_frontier_point.restype = ctypes.c_int64
+        L.oracle_rho.argtypes = [f32p, f32p, f32p, ctypes.c_int64, u8p]
+        L.oracle_rho.restype = ctypes.c_int64
         L.oracle_grid_res.argtypes = [ctypes.c_int64, ctypes.c_int]
         L.oracle_grid_res.restype = ctypes.c_int
         L.oracle_cells.argtypes = [f32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, i32p]
@@ -180,6 +184,17 @@ def frontier_point(d1sq, d2sq, delta, eps_t) -> np.ndarray:
     return out[:k].copy()
 
 
+def rho(d1sq, d2sq, delta) -> np.ndarray:
+    """Flags of the local heuristic rho_i = delta_i / c_i > 1/2 (bool [n])."""
+    d1 = np.ascontiguousarray(d1sq, dtype=np.float32)
+    d2 = np.ascontiguousarray(d2sq, dtype=np.float32)
+    dl = np.ascontiguousarray(delta, dtype=np.float32)
+    out = np.empty(d1.shape[0], np.uint8)
+    lib().oracle_rho(_p(d1, ctypes.c_float), _p(d2, ctypes.c_float), _p(dl, ctypes.c_float), d1.shape[0],
+                     _p(out, ctypes.c_uint8))
+    return out.astype(bool)
+
+
 class ClockState:
     """Cumulative-clock frontier (the per-step cost subsection, Thm A.3): S is
     the running sum of eps_t in FP64.  A certificate last revisited at clock
@@ -275,6 +290,9 @@ class StepResult:
     n_missed: int                 # failed but not detected (Lemma 1: must be 0)
     n_false: int                  # detected but not failed
     med_c: np.float32             # trunc_median of the pre-step clearances
+    rho: np.ndarray               # bool: flagged by the local heuristic rho_i > 1/2
+    n_rho: int                    # flagged points
+    n_rho_hit: int                # flagged points that failed
 
 
 def clearances(cert: Certificates) -> np.ndarray:
@@ -292,10 +310,11 @@ def step(p_old, p_new, cert_old: Certificates, nthreads: int = 0, rule: str = "s
     p_old, p_new = _pos(p_old), _pos(p_new)
     n, dim = p_new.shape
     e = eps(p_old, p_new)
+    delta = disp(p_old, p_new)
     if rule == "step":
         F = frontier(cert_old.d1sq, cert_old.d2sq, e)
     elif rule == "point":
-        F = frontier_point(cert_old.d1sq, cert_old.d2sq, disp(p_old, p_new), e)
+        F = frontier_point(cert_old.d1sq, cert_old.d2sq, delta, e)
     elif rule == "clock":
         F = clock.frontier(e)
     else:
@@ -314,4 +333,9 @@ def step(p_old, p_new, cert_old: Certificates, nthreads: int = 0, rule: str = "s
         eps_t=e, frontier=F, cert=new, failed=failed, cell=cell, g_h=g, H=H, H_cand=Hc,
         m=m, m_cand=mc, C=C, n_failed=int(failed.sum()),
         n_missed=int((failed & ~inF).sum()), n_false=int((inF & ~failed).sum()),
-        med_c=trunc_median(clearances(cert_old)))
+        med_c=trunc_median(clearances(cert_old)), **_rho_audit(cert_old, delta, failed))
+
+
+def _rho_audit(cert_old: Certificates, delta: np.ndarray, failed: np.ndarray) -> dict:
+    r = rho(cert_old.d1sq, cert_old.d2sq, delta)
+    return {"rho": r, "n_rho": int(r.sum()), "n_rho_hit": int((r & failed).sum())}

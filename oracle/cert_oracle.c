@@ -177,6 +177,25 @@ void oracle_disp(const float *p_old, const float *p_new, int64_t n, int dim, flo
  * delta_i + eps (triangle inequality, as in Lemma 1), so the certificate is
  * safe when c_i > 2 (delta_i + eps).  Same rounding guard as oracle_frontier.
  */
+/*
+ * The local heuristic of Sec. 3 and Table 1: point i is flagged when
+ * rho_i = delta_i / c_i > 1/2, delta_i its own displacement and c_i = d2_i - d1_i
+ * its pre-step clearance.  Written as 2 delta_i > c_i, the same comparison of
+ * the FP32 values without rounding a quotient (2 delta_i is exact); c_i = 0
+ * with delta_i = 0 (0/0) is not flagged.  Unlike the rules above it is no
+ * bound: a point that stays put can still lose its nearest neighbour.
+ */
+int64_t oracle_rho(const float *d1sq, const float *d2sq, const float *disp, int64_t n, uint8_t *out)
+{
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        float c = sqrtf(d2sq[i]) - sqrtf(d1sq[i]);
+        out[i] = (uint8_t)(2.0f * disp[i] > c);
+        k += out[i];
+    }
+    return k;
+}
+
 int64_t oracle_frontier_point(const float *d1sq, const float *d2sq, const float *disp, int64_t n, float eps,
                               int32_t *out)
 {

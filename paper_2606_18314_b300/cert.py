@@ -30,7 +30,7 @@ class cert_config(ctypes.Structure):
                 ("offsets", ctypes.POINTER(ctypes.c_int64)), ("n_total", ctypes.c_int64),
                 ("cell_scale", ctypes.c_float), ("policy", ctypes.c_int32),
                 ("bucket_factor", ctypes.c_int32), ("cell_quantile", ctypes.c_float),
-                ("frontier_rule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("frontier_rule", ctypes.c_int32), ("rho_audit", ctypes.c_int32)]
 
 
 class cert_scene_result(ctypes.Structure):
@@ -41,7 +41,8 @@ class cert_scene_result(ctypes.Structure):
                 ("n_searched", ctypes.c_int32), ("failed_cells", ctypes.c_int32),
                 ("frontier_cells", ctypes.c_int32), ("occupied_cells", ctypes.c_int32),
                 ("strategy", ctypes.c_int32), ("pred_inc", ctypes.c_float), ("pred_reb", ctypes.c_float),
-                ("grid_res", ctypes.c_int32), ("search_res", ctypes.c_int32)]
+                ("grid_res", ctypes.c_int32), ("search_res", ctypes.c_int32),
+                ("n_rho", ctypes.c_int32), ("n_rho_hit", ctypes.c_int32)]
 
 
 SCENE_DTYPE = np.dtype([(n, np.dtype(t).newbyteorder("=")) for n, t in [
@@ -50,7 +51,7 @@ SCENE_DTYPE = np.dtype([(n, np.dtype(t).newbyteorder("=")) for n, t in [
     ("n_missed", np.int32), ("n_false", np.int32), ("n_searched", np.int32),
     ("failed_cells", np.int32), ("frontier_cells", np.int32), ("occupied_cells", np.int32),
     ("strategy", np.int32), ("pred_inc", np.float32), ("pred_reb", np.float32),
-    ("grid_res", np.int32), ("search_res", np.int32)]])
+    ("grid_res", np.int32), ("search_res", np.int32), ("n_rho", np.int32), ("n_rho_hit", np.int32)]])
 assert SCENE_DTYPE.itemsize == ctypes.sizeof(cert_scene_result)
 
 
@@ -280,7 +281,7 @@ class Context:
     """
 
     def __init__(self, pos, offsets=None, cell_scale=0.0, policy=CERT_INCREMENTAL, stream=None,
-                 bucket_factor=0, cell_quantile=0.0, frontier_rule="step"):
+                 bucket_factor=0, cell_quantile=0.0, frontier_rule="step", rho_audit=False):
         import torch
         self.dim = int(pos.shape[1])
         self._keep = []
@@ -298,6 +299,7 @@ class Context:
         cfg.bucket_factor = int(bucket_factor)
         cfg.cell_quantile = float(cell_quantile)
         cfg.frontier_rule = FRONTIER_RULE[frontier_rule] if isinstance(frontier_rule, str) else int(frontier_rule)
+        cfg.rho_audit = 1 if rho_audit else 0
         self.n_scenes = cfg.n_scenes
         self.n = cfg.n_total
         h = ctypes.c_void_p()

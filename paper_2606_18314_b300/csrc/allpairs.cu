@@ -276,7 +276,7 @@ __global__ void k_allpairs_merge_step(const APArgs a, const APMergeOut o)
     const StepArgs &sa = o.step;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < sa.n_total;
-    int s = -1, changed = 0, missed = 0, first = 0;
+    int s = -1, changed = 0, missed = 0, first = 0, hit = 0;
     double dl = 0.0;
     if (valid) {
         s = sa.scene_of[i];
@@ -288,7 +288,9 @@ __global__ void k_allpairs_merge_step(const APArgs a, const APMergeOut o)
         changed = n1 != sa.nn[i];
         sa.failed[i] = (uint8_t)changed;
         if (changed) {
-            missed = !sa.inF[i];
+            const uint32_t fl = sa.inF[i];   // bit 0: in F_t, bit 1: rho-flagged
+            missed = !(fl & 1u);
+            hit = (int)(fl >> 1);
             const int old = atomicAdd(&sa.hfail[sp.h_off + sa.hcell[i]], 1);
             first = old == 0;
             dl = nlogn_step(sa.nlogn, old);
@@ -305,12 +307,14 @@ __global__ void k_allpairs_merge_step(const APArgs a, const APMergeOut o)
     const int nc = run_sum_i32(m, changed);
     const int nm = run_sum_i32(m, missed);
     const int fc = run_sum_i32(m, first);
+    const int nh = run_sum_i32(m, hit);
     const double sd = run_sum_f64(m, dl);
     if (s >= 0 && run_leader(m)) {
         atomicAdd(&sa.acc[s].n_searched, nsr);
         if (nc) {
             atomicAdd(&sa.acc[s].n_failed, nc);
             atomicAdd(&sa.acc[s].n_missed, nm);
+            if (nh) atomicAdd(&sa.acc[s].n_rho_hit, nh);
             atomicAdd(&sa.acc[s].failed_cells, fc);
             atomicAdd(&sa.acc[s].s_fail, sd);
         }

@@ -61,7 +61,9 @@ struct SceneAcc {
     int32_t occ;                   // occupied entropy cells (C)
     int32_t n_failed, n_missed;
     int32_t failed_cells, frontier_cells;
-    int32_t n_searched, pad;
+    int32_t n_searched;
+    int32_t n_rho, n_rho_hit;      // local heuristic rho_i > 1/2: flagged, flagged and failed
+    int32_t pad;
     double s_fail;                 // sum over cells of n ln n, failures
     double s_front;                // sum over cells of n ln n, detected frontier
 };

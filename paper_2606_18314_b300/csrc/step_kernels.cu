@@ -214,6 +214,8 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     const int tp = t - a.ntiles_b;
     const int base = tp * kScanTile + threadIdx.x * kScanItems;
     uint32_t f[kScanItems];
+    uint32_t rho = 0u;                 // bit k: item k flagged by the rho heuristic
+    static_assert(kScanItems <= 32, "rho flags fit one word");
     int sc[kScanItems];
     uint32_t sum = 0u;
 #pragma unroll
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
                 const double S_prev = a.st[s].S;
                 double S_i;
                 float c_rev, g_rev;
-                if (a.inF[i]) {
+                if (a.inF[i] & 1u) {
                     S_i = S_prev;
                     c_rev = c;
                     g_rev = __fadd_rn(d1, d2);
@@ -260,7 +262,14 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
                 }
                 f[k] = (c <= __fadd_rn(motion, tau)) ? 1u : 0u;
             }
-            a.inF[i] = (uint8_t)f[k];
+            // the local heuristic of Sec. 3: rho_i = delta_i / c_i > 1/2, taken as
+            // 2 delta_i > c_i on the FP32 values (exact: the doubling rounds nothing)
+            uint32_t r = 0u;
+            if (a.rho_audit) {
+                r = (__fmul_rn(2.0f, __fsqrt_rn(a.pos_new[i].w)) > c) ? 1u : 0u;
+                rho |= r << k;
+            }
+            a.inF[i] = (uint8_t)(f[k] | (r << 1));
         }
         sum += f[k];
     }
@@ -274,7 +283,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     uint32_t run = s_excl + pre;
     // a thread's consecutive points nearly always share one scene: accumulate
     // locally and reduce once per warp; a scene change inside them is flushed directly
-    int cur = -1, acc_first = 0;
+    int cur = -1, acc_first = 0, acc_rho = 0;
     double acc_dl = 0.0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
@@ -282,14 +291,17 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
         const int s = sc[k];
         if (s >= 0) {
             if (s != cur) {
-                if (cur >= 0 && (acc_first || acc_dl != 0.0)) {
+                if (cur >= 0 && (acc_first || acc_dl != 0.0 || acc_rho)) {
                     if (acc_first) atomicAdd(&a.acc[cur].frontier_cells, acc_first);
                     if (acc_dl != 0.0) atomicAdd(&a.acc[cur].s_front, acc_dl);
+                    if (acc_rho) atomicAdd(&a.acc[cur].n_rho, acc_rho);
                 }
                 cur = s;
                 acc_first = 0;
                 acc_dl = 0.0;
+                acc_rho = 0;
             }
+            acc_rho += (int)((rho >> k) & 1u);
             const SceneParams &sp = a.sp[s];
             if (i == sp.pt_off) a.fstart[s] = (int)run;
             if (f[k]) {
@@ -305,9 +317,11 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     const unsigned m = scene_run_mask(cur);
     const int fc = run_sum_i32(m, acc_first);
     const double sd = run_sum_f64(m, acc_dl);
+    const int nr = a.rho_audit ? run_sum_i32(m, acc_rho) : 0;
     if (cur >= 0 && run_leader(m)) {
         if (fc) atomicAdd(&a.acc[cur].frontier_cells, fc);
         if (sd != 0.0) atomicAdd(&a.acc[cur].s_front, sd);
+        if (nr) atomicAdd(&a.acc[cur].n_rho, nr);
     }
 }
 
@@ -521,12 +535,12 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
             }
         }
     }
-    int changed[kScatPer], missed[kScatPer], first[kScatPer];
+    int changed[kScatPer], missed[kScatPer], first[kScatPer], hit[kScatPer];
     double dl[kScatPer];
 #pragma unroll
     for (int k = 0; k < kScatPer; ++k) {
         const int i = base + k * kThreads;
-        changed[k] = missed[k] = first[k] = 0;
+        changed[k] = missed[k] = first[k] = hit[k] = 0;
         dl[k] = 0.0;
         if (s[k] < 0) continue;
         const SceneParams sp = a.sp[s[k]];
@@ -582,7 +596,9 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
                     changed[k] = j1 != na[k];
                     a.failed[i] = (uint8_t)changed[k];
                     if (changed[k]) {
-                        missed[k] = !a.inF[i];
+                        const uint32_t fl = a.inF[i];
+                        missed[k] = !(fl & 1u);
+                        hit[k] = (int)(fl >> 1);
                         const int old = atomicAdd(&a.hfail[sp.h_off + a.hcell[i]], 1);
                         first[k] = old == 0;
                         dl[k] = nlogn_step(a.nlogn, old);
@@ -601,10 +617,12 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
         if (__any_sync(kFull, ncg != 0)) {
             const int nm = run_sum_i32(m, missed[k]);
             const int fc = run_sum_i32(m, first[k]);
+            const int nh = run_sum_i32(m, hit[k]);
             const double sd = run_sum_f64(m, dl[k]);
             if (s[k] >= 0 && run_leader(m) && ncg) {
                 atomicAdd(&a.acc[s[k]].n_failed, ncg);
                 atomicAdd(&a.acc[s[k]].n_missed, nm);
+                if (nh) atomicAdd(&a.acc[s[k]].n_rho_hit, nh);
                 atomicAdd(&a.acc[s[k]].failed_cells, fc);
                 atomicAdd(&a.acc[s[k]].s_fail, sd);
             }
@@ -906,21 +924,23 @@ __device__ __forceinline__ void warp_merge_top4(Top4 &t)
 
 // Certificate write and failure audit of one searched point (thread level).
 struct SearchOut {
-    int changed, missed, first;
+    int changed, missed, first, hit;
     double dl;
 };
 
 __device__ __forceinline__ SearchOut write_certificate(const StepArgs &a, const SceneParams &sp, int gi,
                                                        const Top4 &t, float L)
 {
-    SearchOut o = {0, 0, 0, 0.0};
+    SearchOut o = {0, 0, 0, 0, 0.0};
     const int n1 = (t.j0 != 0x7fffffff) ? t.j0 - sp.pt_off : -1;
     const int n2 = (t.j1 != 0x7fffffff) ? t.j1 - sp.pt_off : -1;
     if (a.mode == MODE_STEP) {
         o.changed = n1 != a.nn[gi];
         a.failed[gi] = (uint8_t)o.changed;
         if (o.changed) {
-            o.missed = !a.inF[gi];
+            const uint32_t fl = a.inF[gi];
+            o.missed = !(fl & 1u);
+            o.hit = (int)(fl >> 1);
             const int old = atomicAdd(&a.hfail[sp.h_off + a.hcell[gi]], 1);
             o.first = old == 0;
             o.dl = nlogn_step(a.nlogn, old);
@@ -962,7 +982,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
         const int e = r0 + (int)threadIdx.x;
         const bool active = e < (int)count;
         int s = -1;
-        SearchOut o = {0, 0, 0, 0.0};
+        SearchOut o = {0, 0, 0, 0, 0.0};
         if (active) {
             const int slot = s_list[e];
             s = a.scene_of[slot];        // slot ranges of scenes equal their point ranges
@@ -1006,12 +1026,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
             const int nc = run_sum_i32(m, o.changed);
             const int nm = run_sum_i32(m, o.missed);
             const int fc = run_sum_i32(m, o.first);
+            const int nh = run_sum_i32(m, o.hit);
             const double sd = run_sum_f64(m, o.dl);
             if (s >= 0 && run_leader(m)) {
                 atomicAdd(&a.acc[s].n_searched, nsr);
                 if (nc) {
                     atomicAdd(&a.acc[s].n_failed, nc);
                     atomicAdd(&a.acc[s].n_missed, nm);
+                    if (nh) atomicAdd(&a.acc[s].n_rho_hit, nh);
                     atomicAdd(&a.acc[s].failed_cells, fc);
                     atomicAdd(&a.acc[s].s_fail, sd);
                 }
@@ -1077,6 +1099,7 @@ __global__ void __launch_bounds__(kThreads) k_far(const StepArgs a)
             if (a.mode == MODE_STEP && o.changed) {
                 atomicAdd(&a.acc[s].n_failed, 1);
                 atomicAdd(&a.acc[s].n_missed, o.missed);
+                if (o.hit) atomicAdd(&a.acc[s].n_rho_hit, 1);
                 atomicAdd(&a.acc[s].failed_cells, o.first);
                 atomicAdd(&a.acc[s].s_fail, o.dl);
             }
@@ -1123,6 +1146,8 @@ __global__ void k_finalize(const StepArgs a)
         r.pred_reb = st.pred_reb;
         r.grid_res = sp.g_h;
         r.search_res = st.g_cur;
+        r.n_rho = acc.n_rho;
+        r.n_rho_hit = acc.n_rho_hit;
         a.res[s] = r;
         if (r.eps_t > __fmul_ru(a.declared_eps, 1.0f + 0x1p-20f)) atomicOr(a.status, ST_EBOUND);
         st.prev_fail_ratio = (float)acc.n_failed / (float)max(1, nF);

@@ -194,6 +194,45 @@ def test_frontier_rules_match_oracle(torch, rule, family):
         ctx.close()
 
 
+@pytest.mark.parametrize("rule", ["step", "point", "clock"])
+def test_rho_audit_matches_oracle(torch, rule):
+    """rho_audit: the flagged count (k_scan) and the flagged failures (counted
+    by the refresh, the search, the far pass and the all-pairs merge) equal the
+    oracle's in every scene of a batch, under every frontier rule and strategy;
+    without the audit both counts stay 0 and nothing else changes."""
+    from paper_2606_18314_b300 import cert
+    m = scenes.BatchMotion.mixed(n_scenes=10, lo=300, hi=3000, eps=2e-3, seed=21)
+    off = m.offsets
+    frames = m.frames(6)
+    ctx = cert.Context(dev(torch, frames[0]), offsets=off, frontier_rule=rule, rho_audit=True)
+    plain = cert.Context(dev(torch, frames[0]), offsets=off, frontier_rule=rule)
+    refs = [oracle.top2(frames[0][off[s]:off[s + 1]]) for s in range(10)]
+    clocks = [oracle.ClockState(r) for r in refs] if rule == "clock" else [None] * 10
+    strategies = ["incremental", "rebuild", "allpairs", "incremental", "rebuild", "incremental"]
+    seen_hits = 0
+    for t in range(1, 7):
+        ctx.step(dev(torch, frames[t]), 2e-3, strategies[t - 1])
+        plain.step(dev(torch, frames[t]), 2e-3, strategies[t - 1])
+        res, _ = ctx.sync()
+        res0, _ = plain.sync()
+        views = ctx.views()
+        for s in range(10):
+            a, b = frames[t - 1][off[s]:off[s + 1]], frames[t][off[s]:off[s + 1]]
+            r = oracle.step(a, b, refs[s], rule=rule, clock=clocks[s])
+            tag = f"{rule} scene {s} step {t}"
+            assert_step_equal(ctx, res, views, r, s=s, tag=tag)
+            assert int(res[s]["n_rho"]) == r.n_rho, (tag, int(res[s]["n_rho"]), r.n_rho)
+            assert int(res[s]["n_rho_hit"]) == r.n_rho_hit, (tag, int(res[s]["n_rho_hit"]), r.n_rho_hit)
+            seen_hits += r.n_rho_hit
+            refs[s] = r.cert
+        assert np.all(res0["n_rho"] == 0) and np.all(res0["n_rho_hit"] == 0)
+        for k in ("n_frontier", "n_failed", "n_missed", "n_false", "failed_cells", "frontier_cells"):
+            assert np.array_equal(res0[k], res[k]), k
+    assert seen_hits > 0
+    ctx.close()
+    plain.close()
+
+
 def test_strategies_agree_bitwise(torch):
     from paper_2606_18314_b300 import cert
     m = scenes.BatchMotion.mixed(n_scenes=5, lo=800, hi=3000, eps=2e-3, seed=7)

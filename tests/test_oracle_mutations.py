@@ -1,6 +1,6 @@
 """Planted mistakes: each mutant of the C oracle (a dropped term, a loosened
-tie-break, a wrong constant, transposed cell axes, a wrong normaliser) must be
-caught by at least one pin.  Mutants are compiled from a text-edited copy in a
+tie-break, a wrong constant, transposed cell axes, a wrong normaliser, a
+loosened comparison) must be caught by at least one pin.  Mutants are compiled from a text-edited copy in a
 temporary directory; the committed oracle is never touched."""
 import ctypes
 import os
@@ -12,6 +12,7 @@ import pytest
 import oracle
 from tests import test_oracle_core as pins
 from tests import test_oracle_frontier_rules as rules
+from tests import test_oracle_rho as rho
 
 MUTANTS = {
     "drop_dz": ("s = s + dz * dz;", "s = s;"),
@@ -22,6 +23,9 @@ MUTANTS = {
     "eps_first_point": ("if (D > m)\n            m = D;", "if (i == 0)\n            m = D;"),
     "point_budget_halved": ("float rhs = 2.0f * (disp[i] + eps) + tau;", "float rhs = (disp[i] + eps) + tau;"),
     "point_budget_own_only": ("float rhs = 2.0f * (disp[i] + eps) + tau;", "float rhs = 2.0f * disp[i] + tau;"),
+    "rho_no_factor": ("out[i] = (uint8_t)(2.0f * disp[i] > c);", "out[i] = (uint8_t)(disp[i] > c);"),
+    "rho_not_strict": ("out[i] = (uint8_t)(2.0f * disp[i] > c);", "out[i] = (uint8_t)(2.0f * disp[i] >= c);"),
+    "rho_squared_clearance": ("float c = sqrtf(d2sq[i]) - sqrtf(d1sq[i]);", "float c = d2sq[i] - d1sq[i];"),
 }
 
 PIN_CALLS = [
@@ -37,6 +41,8 @@ PIN_CALLS = [
     lambda o: rules.test_point_and_clock_rules_never_miss("adversarial_crossing", 3),
     lambda o: rules.test_point_and_clock_rules_never_miss("clustered_drift", 2),
     lambda o: rules.test_point_rule_leaves_out_a_static_point_with_clearance_three_eps(),
+    lambda o: rho.test_rho_dyadic_closed_forms(),
+    lambda o: rho.test_rho_step_level_dyadic(),
 ]
 
 
