@@ -24,6 +24,10 @@ Nearest-Neighbour Structures"):
 * ``step`` -- one maintenance step end to end (Algorithm 1 with every
   certificate recomputed from scratch, which is the exact result Cor. A.2 says
   the repair reaches), plus the failure audit of Table 1.
+* ``knn`` (module ``oracle.knn``) -- k-nearest-neighbour certificates, the
+  k = 2 certificate one rank further out (Sec. 6 leaves kNN graphs open):
+  brute-force top-(k+1) lists, the frontier d_{k+1} - d_k <= 4 eps_t + tau
+  (Lemma 1's argument at rank k) and set-valued failures.
 * ``trunc_median`` -- the lower median truncated to 3 mantissa bits, the
   definition the selector features use (no paper counterpart).
 """
@@ -77,6 +81,8 @@ def lib():
         L.oracle_disp.restype = None
         L.oracle_frontier_point.argtypes = [f32p, f32p, f32p, ctypes.c_int64, ctypes.c_float, i32p]
         L.oracle_frontier_point.restype = ctypes.c_int64
+        L.oracle_knn.argtypes = [f32p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, i32p, f32p, ctypes.c_int]
+        L.oracle_knn.restype = ctypes.c_int
         L.oracle_rho.argtypes = [f32p, f32p, f32p, ctypes.c_int64, u8p]
         L.oracle_rho.restype = ctypes.c_int64
         L.oracle_grid_res.argtypes = [ctypes.c_int64, ctypes.c_int]

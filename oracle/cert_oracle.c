@@ -107,6 +107,52 @@ int oracle_top2(const float *pos, int64_t n, int dim, int32_t *nn, float *d1sq,
     return 0;
 }
 
+/*
+ * The m nearest of point i over every j != i, ascending in the key (D, j):
+ * the k-nearest-neighbour certificate one rank further out (the k = 2
+ * certificate of Def. 1 is m = 2).  Candidates are visited in ascending j
+ * and placed behind every stored key that is <= theirs, so equal D keep
+ * the lower index first.  m <= 32.
+ */
+static void knn_one(const float *pos, int64_t n, int dim, int64_t i, int m, int32_t *idx, float *d2)
+{
+    float bd[32];
+    int32_t bj[32];
+    int have = 0;
+    const float *pi = pos + i * dim;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i)
+            continue;
+        float D = sq_dist(pi, pos + j * dim, dim);
+        if (have == m && !(D < bd[m - 1]))
+            continue;
+        int s = have < m ? have++ : m - 1;
+        while (s > 0 && D < bd[s - 1]) {
+            bd[s] = bd[s - 1];
+            bj[s] = bj[s - 1];
+            --s;
+        }
+        bd[s] = D;
+        bj[s] = (int32_t)j;
+    }
+    for (int r = 0; r < m; ++r) {
+        idx[i * m + r] = bj[r];
+        d2[i * m + r] = bd[r];
+    }
+}
+
+/* The m nearest of every point, [n][m] row-major.  1 <= m <= 32, n > m.  Returns 0. */
+int oracle_knn(const float *pos, int64_t n, int dim, int m, int32_t *idx, float *d2, int nthreads)
+{
+    if (m < 1 || m > 32 || n <= m || (dim != 2 && dim != 3))
+        return -1;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i)
+        knn_one(pos, n, dim, i, m, idx, d2);
+    return 0;
+}
+
 /* Certificates of the listed query points only (a sample of a large scene). */
 int oracle_top2_queries(const float *pos, int64_t n, int dim, const int32_t *q,
                         int64_t nq, int32_t *nn, float *d1sq, float *d2sq,

@@ -23,7 +23,7 @@ def sources():
 
 def deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        [os.path.join(os.path.dirname(HERE), "include", "cert.h")]
+        glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h"))
 
 
 def stale() -> bool:

@@ -55,6 +55,26 @@ SCENE_DTYPE = np.dtype([(n, np.dtype(t).newbyteorder("=")) for n, t in [
 assert SCENE_DTYPE.itemsize == ctypes.sizeof(cert_scene_result)
 
 
+class cert_knn_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("k", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("cell_scale", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+class cert_knn_result(ctypes.Structure):
+    _fields_ = [("eps_t", ctypes.c_float), ("n_frontier", ctypes.c_int32), ("n_failed", ctypes.c_int32),
+                ("n_missed", ctypes.c_int32), ("n_false", ctypes.c_int32), ("n_searched", ctypes.c_int32),
+                ("grid_res", ctypes.c_int32), ("strategy", ctypes.c_int32)]
+
+
+KNN_RESULT_FIELDS = [f for f, _ in cert_knn_result._fields_]
+
+
+class cert_knn_views(ctypes.Structure):
+    _fields_ = [("idx", ctypes.c_void_p), ("d2", ctypes.c_void_p), ("frontier", ctypes.c_void_p),
+                ("failed", ctypes.c_void_p), ("result", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("k", ctypes.c_int32), ("dim", ctypes.c_int32)]
+
+
 class cert_views(ctypes.Structure):
     _fields_ = [("nn", ctypes.c_void_p), ("d1sq", ctypes.c_void_p), ("d2sq", ctypes.c_void_p),
                 ("cell", ctypes.c_void_p), ("frontier", ctypes.c_void_p), ("failed", ctypes.c_void_p),
@@ -65,7 +85,8 @@ class cert_views(ctypes.Structure):
 _lib = None
 
 # every symbol include/cert.h declares (checked by the CPU tests)
-EXPORTS = ["cert_init", "cert_step", "cert_step_host", "cert_step_host_stream", "cert_rebuild", "cert_get_views",
+EXPORTS = ["cert_knn_init", "cert_knn_step", "cert_knn_get_views", "cert_knn_sync_result", "cert_knn_destroy",
+           "cert_init", "cert_step", "cert_step_host", "cert_step_host_stream", "cert_rebuild", "cert_get_views",
            "cert_sync_result", "cert_distances", "cert_allpairs", "cert_destroy", "cert_last_error",
            "cert_version", "cert_profile_begin", "cert_profile_end",
            "cert_allpairs_noalloc", "cert_set_cell_scale", "cert_set_cell_quantile", "cert_get_cell_scale", "cert_autotune",
@@ -127,6 +148,14 @@ def lib():
     for name in ["cert_init", "cert_step", "cert_step_host", "cert_rebuild", "cert_get_views",
                  "cert_sync_result", "cert_distances", "cert_allpairs", "cert_profile_begin",
                  "cert_profile_end"]:
+        getattr(L, name).restype = ctypes.c_int
+    L.cert_knn_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(cert_knn_config), vp, vp]
+    L.cert_knn_step.argtypes = [vp, vp, f32, i32, vp]
+    L.cert_knn_get_views.argtypes = [vp, ctypes.POINTER(cert_knn_views)]
+    L.cert_knn_sync_result.argtypes = [vp, vp]
+    L.cert_knn_destroy.argtypes = [vp]
+    L.cert_knn_destroy.restype = None
+    for name in ["cert_knn_init", "cert_knn_step", "cert_knn_get_views", "cert_knn_sync_result"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -450,3 +479,58 @@ class Context:
         assert p.shape == (MLP_PARAMS,) and nm.shape == (16,)
         _check(lib().cert_selector_load(self.h, ctypes.c_void_p(p.ctypes.data), ctypes.c_void_p(nm.ctypes.data)),
                self.h)
+
+
+class KnnContext:
+    """k-nearest-neighbour certificates of one point set (include/cert_knn.h).
+
+    ``KnnContext(pos, k)`` calls ``cert_knn_init`` (exact k+1 nearest of every
+    point); ``step`` calls ``cert_knn_step``; ``views`` gives the lists as
+    torch tensors [k+1][n] (rank-major, valid until the next call) and the
+    frontier / failure flags; ``sync`` returns the step's scalars as a dict.
+    """
+
+    def __init__(self, pos, k, cell_scale=0.0, stream=None):
+        cfg = cert_knn_config()
+        cfg.dim = int(pos.shape[1])
+        cfg.k = int(k)
+        cfg.n = int(pos.shape[0])
+        cfg.cell_scale = float(cell_scale)
+        self.dim, self.k, self.n = cfg.dim, cfg.k, cfg.n
+        h = ctypes.c_void_p()
+        _check(lib().cert_knn_init(ctypes.byref(h), ctypes.byref(cfg), _dev_ptr(pos, "torch.float32", self.dim),
+                                   _stream_ptr(stream)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cert_knn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, pos_new, eps, strategy=CERT_INCREMENTAL, stream=None):
+        if isinstance(strategy, str):
+            strategy = STRATEGY[strategy]
+        if pos_new.shape[0] != self.n:
+            raise ValueError("positions do not match the context's point count")
+        _check(lib().cert_knn_step(self.h, _dev_ptr(pos_new, "torch.float32", self.dim), float(eps), int(strategy),
+                                   _stream_ptr(stream)))
+
+    def views(self):
+        v = cert_knn_views()
+        _check(lib().cert_knn_get_views(self.h, ctypes.byref(v)))
+        n, k1 = int(v.n), int(v.k) + 1
+        return {"idx": _view(v.idx, (k1, n), "<i4", self), "d2": _view(v.d2, (k1, n), "<f4", self),
+                "frontier": _view(v.frontier, (n,), "|u1", self), "failed": _view(v.failed, (n,), "|u1", self)}
+
+    def sync(self, raise_on_status=True):
+        r = cert_knn_result()
+        rc = lib().cert_knn_sync_result(self.h, ctypes.byref(r))
+        if raise_on_status:
+            _check(rc)
+        return {f: getattr(r, f) for f in KNN_RESULT_FIELDS}, rc

@@ -106,3 +106,30 @@ def test_python_modules_import_without_gpu():
     assert p.shape == (4866,) and p.dtype.name == "float32"
     assert abs(float(p[:512].std()) - (2.0 / 8) ** 0.5) < 0.1     # He-normal fan-in 8
     assert float(abs(p[512:576]).max()) == 0.0                       # zero biases
+
+
+def test_knn_rejects_bad_arguments_without_a_gpu(L):
+    from paper_2606_18314_b300 import cert
+    h = ctypes.c_void_p()
+    cfg = cert.cert_knn_config()
+    cfg.dim, cfg.k, cfg.n = 3, 4, 100
+
+    def init():
+        return L.cert_knn_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None)
+
+    for field, bad, good, word in [("dim", 4, 3, b"dim"), ("k", 0, 4, b"k must"), ("k", 17, 4, b"k must"),
+                                   ("n", 5, 100, b"n must"), ("cell_scale", -1.0, 0.0, b"cell_scale"),
+                                   ("cell_scale", float("inf"), 0.0, b"cell_scale"), ("reserved", 1, 0, b"reserved")]:
+        setattr(cfg, field, bad)
+        assert init() == cert.CERT_EINVAL, field
+        assert word in L.cert_last_error(None), field
+        assert h.value is None
+        setattr(cfg, field, good)
+    assert L.cert_knn_init(ctypes.byref(h), ctypes.byref(cfg), None, None) == cert.CERT_EINVAL
+    assert L.cert_knn_step(None, ctypes.c_void_p(16), ctypes.c_float(1e-3), 1, None) == cert.CERT_EINVAL
+    assert L.cert_knn_sync_result(None, None) == cert.CERT_EINVAL
+    assert L.cert_knn_get_views(None, None) == cert.CERT_EINVAL
+    L.cert_knn_destroy(None)
+    assert ctypes.sizeof(cert.cert_knn_config) == 24
+    assert ctypes.sizeof(cert.cert_knn_result) == 32
+    assert ctypes.sizeof(cert.cert_knn_views) == 5 * 8 + 8 + 4 + 4

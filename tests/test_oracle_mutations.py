@@ -12,6 +12,7 @@ import pytest
 import oracle
 from tests import test_oracle_core as pins
 from tests import test_oracle_frontier_rules as rules
+from tests import test_oracle_knn as knn
 from tests import test_oracle_rho as rho
 
 MUTANTS = {
@@ -26,6 +27,8 @@ MUTANTS = {
     "rho_no_factor": ("out[i] = (uint8_t)(2.0f * disp[i] > c);", "out[i] = (uint8_t)(disp[i] > c);"),
     "rho_not_strict": ("out[i] = (uint8_t)(2.0f * disp[i] > c);", "out[i] = (uint8_t)(2.0f * disp[i] >= c);"),
     "rho_squared_clearance": ("float c = sqrtf(d2sq[i]) - sqrtf(d1sq[i]);", "float c = d2sq[i] - d1sq[i];"),
+    "knn_tie_le": ("while (s > 0 && D < bd[s - 1]) {", "while (s > 0 && D <= bd[s - 1]) {"),
+    "knn_keeps_equal_last": ("if (have == m && !(D < bd[m - 1]))", "if (have == m && D > bd[m - 1])"),
 }
 
 PIN_CALLS = [
@@ -43,6 +46,10 @@ PIN_CALLS = [
     lambda o: rules.test_point_rule_leaves_out_a_static_point_with_clearance_three_eps(),
     lambda o: rho.test_rho_dyadic_closed_forms(),
     lambda o: rho.test_rho_step_level_dyadic(),
+    lambda o: knn.test_knn_matches_exact_rational_bruteforce(17, 3, 2),
+    lambda o: knn.test_knn_matches_a_lexsort_of_the_distance_matrix(3),
+    lambda o: knn.test_knn_tightness_at_rank_three(True),
+    lambda o: knn.test_knn_tightness_at_rank_three(False),
 ]
 
 
