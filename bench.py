@@ -280,6 +280,66 @@ def graph_loop(ctx, dev_frames, F, eps, strategy, K, use_graph, stream, torch):
     return e0.elapsed_time(e1), K
 
 
+def knn_phase_bytes(ph, n, dim, k, cells, n_searched, n_refreshed):
+    """Compulsory DRAM bytes of one kNN step phase (lists are [k+1][n] int32 + float32)."""
+    K1 = k + 1
+    if ph == "prepare":      # read input + old position, write position, cell, rank; the cell counters
+        return n * (4 * dim + 40) + 8 * cells
+    if ph == "scan":         # read the counts, write the starts, zero the counts
+        return 12 * cells
+    if ph == "refresh":      # cell, rank, start, position, scatter; frontier ranks; list read; refreshed writes
+        return n * (58 + 4 * K1) + n_refreshed * (8 * K1 + 5)
+    if ph == "search":       # list entry, position, old k indices, new list, L, flags
+        return n_searched * (26 + 4 * k + 8 * K1)
+    return 0
+
+
+def knn_report(cert, torch, steps, peaks, stream):
+    """k-nearest-neighbour certificates (the richer certificates the paper
+    leaves open): point-updates/s with the steps replayed from a CUDA graph,
+    per-phase times from CUDA events, and the roofline of the dominant phase."""
+    out = {"peak_gbs": peaks["hbm_gbs"], "rows": []}
+    cases = [("uniform_clusters", 262144, 3, 1e-4, (1, 4, 8, 16)), ("uniform_brownian", 2097152, 3, 1e-4, (8,))]
+    for family, n, dim, eps, ks in cases:
+        m = scenes.Motion(family, n, dim, eps, seed=1, steps=100)
+        F = 3
+        dev_frames = torch.from_numpy(m.frames(F)).cuda()
+        for k in ks:
+            row = {"workload": f"{family}-{n}-d{dim}", "n": n, "k": k, "eps": eps}
+            for name in ("incremental", "rebuild"):
+                ctx = cert.KnnContext(dev_frames[0], k)
+                for j in range(2 * F):
+                    ctx.step(dev_frames[cycle_index(j, F)], eps, name)
+                ms, _ = graph_loop(ctx, dev_frames, F, eps, cert.STRATEGY[name], max(2 * F, steps), True, stream,
+                                   torch)
+                K = max(2 * F, steps) // (2 * F) * (2 * F)
+                row[name] = {"point_updates_per_s": n * K / (ms / 1e3), "ms_per_step": ms / K}
+                # phase times over one cycle, eager, from the same state
+                ph = {p: 0.0 for p in cert.KnnContext.KNN_PHASES}
+                cnt = np.zeros(4)
+                for j in range(2 * F):
+                    t = ctx.profile(dev_frames[cycle_index(j, F)], eps, name)
+                    r, _ = ctx.sync()
+                    assert r["n_missed"] == 0, "kNN safety rule missed a failure"
+                    for p_ in ph:
+                        ph[p_] += t[p_] / (2 * F)
+                    cnt += [r["n_frontier"], r["n_failed"], r["n_searched"], r["grid_res"]]
+                cnt /= 2 * F
+                cells = int(cnt[3]) ** dim
+                phases = {}
+                for p_, t_ms in ph.items():
+                    b = knn_phase_bytes(p_, n, dim, k, cells, cnt[2], n - cnt[2] if name == "incremental" else 0)
+                    phases[p_] = {"ms": t_ms, "bytes": b, "gbs": b / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0}
+                dom = max((p_ for p_ in phases if p_ != "finalize"), key=lambda p_: phases[p_]["ms"])
+                row[name].update({"frontier_frac": cnt[0] / n, "failed_frac": cnt[1] / n, "searched_frac": cnt[2] / n,
+                                  "grid_res": int(cnt[3]), "phases": phases, "dominant": dom,
+                                  "roofline_frac": phases[dom]["gbs"] / peaks["hbm_gbs"]})
+                ctx.close()
+            out["rows"].append(row)
+        del dev_frames
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,6 +364,8 @@ def main():
     ap.add_argument("--rule-steps", type=int, default=32, help="steps per frontier rule in the detection report")
     ap.add_argument("--matched-steps", type=int, default=48,
                     help="transitions surveyed per scene in the matched-pair entropy experiment (0: skip)")
+    ap.add_argument("--knn-steps", type=int, default=240,
+                    help="graph-replayed steps per k-nearest-neighbour case (0: skip)")
     ap.add_argument("--compare-steps", type=int, default=256)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -480,6 +542,11 @@ def main():
         from paper_2606_18314_b300 import matched
         matched_pair = matched.run(cert, steps=args.matched_steps)
 
+    # ---- k-nearest-neighbour certificates (one scene per context)
+    knn = None
+    if args.knn_steps > 0 and rank == 0:
+        knn = knn_report(cert, torch, args.knn_steps, load_peaks()[0], stream)
+
     # ---- per-phase timing (CUDA events on the launching stream), same workload, eager
     P = max(1, args.prof_steps)
     ctx.profile_begin(P)
@@ -598,7 +665,7 @@ def main():
                 "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
                 "step_counts": step_counts, "compare": compare, "regret": regret, "frontier_rules": rules,
-                "matched_pair": matched_pair, "allpairs": allpairs,
+                "matched_pair": matched_pair, "knn": knn, "allpairs": allpairs,
                 "status": cert.STATUS_NAMES[rc] if 0 <= rc < len(cert.STATUS_NAMES) else rc}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -49,9 +49,11 @@ typedef struct {
     int32_t dim;          /* 2 or 3                                                     */
     int32_t k;            /* neighbours per point, 1 .. CERT_KNN_MAX_K                  */
     int64_t n;            /* points, k + 2 <= n < 2^31                                   */
-    float cell_scale;     /* grid cell side = cell_scale * ((k + 1) / n)^(1/dim): about
-                             cell_scale^dim (k + 1) points per cell when uniform
-                             (0 -> 1.0); the grid has at most 2^24 cells               */
+    float cell_scale;     /* grid cell side = cell_scale x the median (k+1)-th distance of
+                             a 1024-point sample of the previous step (0 -> 1.0); the
+                             first grid assumes a uniform set in the unit domain.  The
+                             grid is hashed into next_pow2(n) buckets (at most 2^24),
+                             so any resolution up to 2048 cells per axis fits          */
     int32_t reserved;     /* must be zero                                               */
 } cert_knn_config;
 
@@ -63,14 +65,18 @@ typedef struct {
     int32_t n_failed;     /* #{i : the set of the k nearest of i changed}                */
     int32_t n_missed;     /* failed but not in the frontier (Lemma 1: always 0)          */
     int32_t n_false;      /* in the frontier but not failed                               */
-    int32_t n_searched;   /* certificates recomputed by a grid search this step          */
-    int32_t grid_res;     /* grid cells per axis                                          */
+    int32_t n_searched;   /* certificates recomputed by a search this step (grid or, for
+                             the few whose box would be too large, every point)       */
+    int32_t grid_res;     /* grid cells per axis (the fine level)                         */
     int32_t strategy;     /* CERT_INCREMENTAL or CERT_REBUILD                              */
+    int32_t grid_res_coarse; /* cells per axis of the coarse level, 0 when the grid had one  */
+    int32_t n_far;        /* searches whose box was too large, done over every point       */
 } cert_knn_result;
 
 /* Device views, valid until the next call on the context.  The lists are
  * rank-major: entry r of point i is at [r * n + i]; ranks 0 .. k hold the
- * k nearest and the (k+1)-th, which fixes the clearance. */
+ * k nearest and the (k+1)-th, which fixes the clearance (two further ranks
+ * follow in the same arrays: spare candidates for the refresh, not exact). */
 typedef struct {
     const int32_t *idx;      /* [k+1][n] neighbour indices, ascending key (D, j)      */
     const float *d2;         /* [k+1][n] their squared distances                       */
@@ -96,6 +102,13 @@ cert_status cert_knn_init(cert_knn_ctx **out, const cert_knn_config *cfg, const 
  * eps is the declared bound (>= 0, finite); eps_t > eps (1 + 2^-20) only
  * latches CERT_EBOUND.  Other strategies are rejected (CERT_EINVAL). */
 cert_status cert_knn_step(cert_knn_ctx *ctx, const float *d_pos_new, float eps, int32_t strategy, void *stream);
+
+/* Diagnostics: the same step as cert_knn_step, with CUDA events between its
+ * phases; synchronises and writes the phase times in ms to h_ms[5]: prepare
+ * (displacement, eps_t, cells), scan (cell starts), refresh (scatter,
+ * frontier, O(k) refresh), search, finalize.  Not capturable. */
+cert_status cert_knn_profile(cert_knn_ctx *ctx, const float *d_pos_new, float eps, int32_t strategy, float *h_ms,
+                             void *stream);
 
 /* Pointers to the current lists and flags (no device work). */
 cert_status cert_knn_get_views(const cert_knn_ctx *ctx, cert_knn_views *out);

@@ -63,7 +63,8 @@ class cert_knn_config(ctypes.Structure):
 class cert_knn_result(ctypes.Structure):
     _fields_ = [("eps_t", ctypes.c_float), ("n_frontier", ctypes.c_int32), ("n_failed", ctypes.c_int32),
                 ("n_missed", ctypes.c_int32), ("n_false", ctypes.c_int32), ("n_searched", ctypes.c_int32),
-                ("grid_res", ctypes.c_int32), ("strategy", ctypes.c_int32)]
+                ("grid_res", ctypes.c_int32), ("strategy", ctypes.c_int32), ("grid_res_coarse", ctypes.c_int32),
+                ("n_far", ctypes.c_int32)]
 
 
 KNN_RESULT_FIELDS = [f for f, _ in cert_knn_result._fields_]
@@ -86,6 +87,7 @@ _lib = None
 
 # every symbol include/cert.h declares (checked by the CPU tests)
 EXPORTS = ["cert_knn_init", "cert_knn_step", "cert_knn_get_views", "cert_knn_sync_result", "cert_knn_destroy",
+           "cert_knn_profile",
            "cert_init", "cert_step", "cert_step_host", "cert_step_host_stream", "cert_rebuild", "cert_get_views",
            "cert_sync_result", "cert_distances", "cert_allpairs", "cert_destroy", "cert_last_error",
            "cert_version", "cert_profile_begin", "cert_profile_end",
@@ -152,10 +154,11 @@ def lib():
     L.cert_knn_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(cert_knn_config), vp, vp]
     L.cert_knn_step.argtypes = [vp, vp, f32, i32, vp]
     L.cert_knn_get_views.argtypes = [vp, ctypes.POINTER(cert_knn_views)]
+    L.cert_knn_profile.argtypes = [vp, vp, f32, i32, vp, vp]
     L.cert_knn_sync_result.argtypes = [vp, vp]
     L.cert_knn_destroy.argtypes = [vp]
     L.cert_knn_destroy.restype = None
-    for name in ["cert_knn_init", "cert_knn_step", "cert_knn_get_views", "cert_knn_sync_result"]:
+    for name in ["cert_knn_init", "cert_knn_step", "cert_knn_get_views", "cert_knn_sync_result", "cert_knn_profile"]:
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -520,6 +523,17 @@ class KnnContext:
             raise ValueError("positions do not match the context's point count")
         _check(lib().cert_knn_step(self.h, _dev_ptr(pos_new, "torch.float32", self.dim), float(eps), int(strategy),
                                    _stream_ptr(stream)))
+
+    KNN_PHASES = ("prepare", "scan", "refresh", "search", "finalize")
+
+    def profile(self, pos_new, eps, strategy=CERT_INCREMENTAL, stream=None):
+        """cert_knn_profile: one step with per-phase CUDA events (synchronises); ms per phase."""
+        if isinstance(strategy, str):
+            strategy = STRATEGY[strategy]
+        ms = np.zeros(5, np.float32)
+        _check(lib().cert_knn_profile(self.h, _dev_ptr(pos_new, "torch.float32", self.dim), float(eps),
+                                      int(strategy), ctypes.c_void_p(ms.ctypes.data), _stream_ptr(stream)))
+        return dict(zip(self.KNN_PHASES, [float(x) for x in ms]))
 
     def views(self):
         v = cert_knn_views()

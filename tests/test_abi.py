@@ -131,5 +131,5 @@ def test_knn_rejects_bad_arguments_without_a_gpu(L):
     assert L.cert_knn_get_views(None, None) == cert.CERT_EINVAL
     L.cert_knn_destroy(None)
     assert ctypes.sizeof(cert.cert_knn_config) == 24
-    assert ctypes.sizeof(cert.cert_knn_result) == 32
+    assert ctypes.sizeof(cert.cert_knn_result) == 40
     assert ctypes.sizeof(cert.cert_knn_views) == 5 * 8 + 8 + 4 + 4
