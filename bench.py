@@ -280,17 +280,27 @@ def graph_loop(ctx, dev_frames, F, eps, strategy, K, use_graph, stream, torch):
     return e0.elapsed_time(e1), K
 
 
-def knn_phase_bytes(ph, n, dim, k, cells, n_searched, n_refreshed):
-    """Compulsory DRAM bytes of one kNN step phase (lists are [k+1][n] int32 + float32)."""
-    K1 = k + 1
-    if ph == "prepare":      # read input + old position, write position, cell, rank; the cell counters
-        return n * (4 * dim + 40) + 8 * cells
-    if ph == "scan":         # read the counts, write the starts, zero the counts
-        return 12 * cells
-    if ph == "refresh":      # cell, rank, start, position, scatter; frontier ranks; list read; refreshed writes
-        return n * (58 + 4 * K1) + n_refreshed * (8 * K1 + 5)
-    if ph == "search":       # list entry, position, old k indices, new list, L, flags
-        return n_searched * (26 + 4 * k + 8 * K1)
+def knn_buckets(n):
+    """Hashed-grid buckets per level of a kNN context: next_pow2(n), at most 2^23."""
+    T = 1
+    while T < n and T < (1 << 23):
+        T <<= 1
+    return T
+
+
+def knn_phase_bytes(ph, n, dim, k, buckets, n_searched, n_refreshed):
+    """Compulsory DRAM bytes of one kNN step phase.  The certificate keeps
+    S = k + 3 ranks (int32 index + float32 key each) in [S][n] arrays; the
+    bucket counters and starts cover both grid levels (2T)."""
+    S = k + 3
+    if ph == "prepare":      # read input + old position, write position, bucket, rank; the counters once
+        return n * (4 * dim + 40) + 8 * buckets
+    if ph == "scan":         # read the counts twice, write the starts, zero the counts
+        return 16 * buckets
+    if ph == "refresh":      # bucket, rank, start, position, scatter; frontier ranks; list read; refreshed writes
+        return n * (58 + 4 * S) + n_refreshed * (8 * S + 5)
+    if ph == "search":       # list entry, position, hint, old k indices, new list, L, flag
+        return n_searched * (29 + 4 * k + 8 * S)
     return 0
 
 
@@ -325,10 +335,10 @@ def knn_report(cert, torch, steps, peaks, stream):
                         ph[p_] += t[p_] / (2 * F)
                     cnt += [r["n_frontier"], r["n_failed"], r["n_searched"], r["grid_res"]]
                 cnt /= 2 * F
-                cells = int(cnt[3]) ** dim
+                buckets = 2 * knn_buckets(n)
                 phases = {}
                 for p_, t_ms in ph.items():
-                    b = knn_phase_bytes(p_, n, dim, k, cells, cnt[2], n - cnt[2] if name == "incremental" else 0)
+                    b = knn_phase_bytes(p_, n, dim, k, buckets, cnt[2], n - cnt[2] if name == "incremental" else 0)
                     phases[p_] = {"ms": t_ms, "bytes": b, "gbs": b / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0}
                 dom = max((p_ for p_ in phases if p_ != "finalize"), key=lambda p_: phases[p_]["ms"])
                 row[name].update({"frontier_frac": cnt[0] / n, "failed_frac": cnt[1] / n, "searched_frac": cnt[2] / n,
