@@ -21,7 +21,9 @@
  * unit domain, points outside it clamped into the boundary cells; FP32 fixed
  * order distances; lowest index first among equal keys; stream-ordered calls
  * that never synchronise unless documented; argument errors returned at once,
- * device conditions latched and returned by cert_knn_sync_result).
+ * device conditions latched and returned by cert_knn_sync_result).  A
+ * context has no error text of its own: after a failed call,
+ * cert_last_error(NULL) gives the calling thread's last message.
  *
  * A context holds one point set (one scene).  Everything it allocates is
  * allocated by cert_knn_init; cert_knn_step allocates nothing, never

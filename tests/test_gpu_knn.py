@@ -173,3 +173,23 @@ def test_eps_bound_and_nonfinite_are_latched(cert):
     with pytest.raises(cert.CertError):
         ctx.step(dev(p), 1e-3, "allpairs")
     ctx.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("k", [1, 3, 16])
+def test_minimum_point_count_steps(cert, k, dim):
+    """n = k + 2: every list holds all other points but one, and the spare
+    ranks cannot all be filled."""
+    n = k + 2
+    rng = np.random.default_rng(40 + k + dim)
+    p = rng.random((n, dim)).astype(np.float32)
+    ctx = cert.KnnContext(dev(p), k)
+    ref = K.cert(p, k)
+    assert_lists(ctx, ref, "init")
+    for t, strategy in enumerate(["incremental", "rebuild", "incremental", "incremental"]):
+        q = (p + rng.uniform(-1e-2, 1e-2, p.shape)).astype(np.float32)
+        ctx.step(dev(q), 0.03, strategy)
+        r = K.step(p, q, ref)
+        assert_step(ctx, r, f"n={n} step {t}")
+        p, ref = q, r.cert
+    ctx.close()
