@@ -74,7 +74,7 @@ def phase_bytes(ph, N, dim, n_buckets, n_front, n_searched, zero_bytes, n_tried=
 # DRAM bytes (read + write) per k_search launch from the ncu capture of the batched
 # 512-scene incremental step (profiles/k_search_batched_512_incremental.md); valid for
 # that workload and kernel version only.
-SEARCH_TRAFFIC_BATCHED = 173.04e6
+SEARCH_TRAFFIC_BATCHED = 173.18e6
 
 
 def load_peaks():
@@ -598,7 +598,7 @@ def main():
     E = max(1, min(args.e2e_steps, K))
     host_frames = torch.from_numpy(frames).pin_memory()
     # pinned result buffer: a copy into pageable memory would block the host each step
-    out_pinned = torch.zeros(E * S * cert.SCENE_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    out_pinned = torch.zeros(max(E, 2) * S * cert.SCENE_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
     out = out_pinned.numpy().view(cert.SCENE_DTYPE)
     row_bytes = N * dim * 4
     base_ptr = host_frames.data_ptr()
