@@ -525,7 +525,7 @@ def main():
         rules = {}
         for rule in ("step", "point", "clock"):
             c3 = cert.Context(dev_frames[0], offsets=offsets, frontier_rule=rule, cell_scale=ctx.cell_scale(),
-                              rho_audit=True)
+                              audit="rho")
             tot = np.zeros(6)
             for k in range(1, args.rule_steps + 1):
                 c3.step(dev_frames[cycle_index(k, F)], eps, cert.CERT_INCREMENTAL)

@@ -98,10 +98,21 @@ typedef struct {
     float cell_quantile;      /* reference d2 = this quantile of a scene's previous d2
                                  over its first min(n,1024) points, in (0,1] (0 -> 0.5) */
     int32_t frontier_rule;    /* cert_frontier_rule (0 -> CERT_FRONTIER_STEP)          */
-    int32_t rho_audit;        /* 1: count the local heuristic rho_i = delta_i / c_i > 1/2
-                                 of Sec. 3 each step (n_rho, n_rho_hit); 0: off, both
-                                 counts 0.  Other values are rejected.                   */
+    int32_t audit;            /* cert_audit flags (0: none); other bits are rejected     */
 } cert_config;
+
+/* Optional per-step audits (cert_config.audit, OR-ed).  Off, their fields of
+ * cert_scene_result stay 0 and the step does no extra work.
+ *   CERT_AUDIT_RHO       the local heuristic rho_i = delta_i / c_i > 1/2 of Sec. 3
+ *                        and Table 1: n_rho, n_rho_hit.
+ *   CERT_AUDIT_GEOMETRY  the spatial spread of the true failures, the frontier
+ *                        descriptors of the paper's transition log (Sec. 6 dataset
+ *                        columns, which the paper names but does not define):
+ *                        gyration and compactness. */
+typedef enum {
+    CERT_AUDIT_RHO = 1,
+    CERT_AUDIT_GEOMETRY = 2
+} cert_audit;
 
 /* Per-scene scalars of the last step.  Same layout on device and host. */
 typedef struct {
@@ -124,11 +135,19 @@ typedef struct {
     float pred_reb;           /* selector output: predicted ln step time, rebuild               */
     int32_t grid_res;         /* entropy-grid cells per axis (smallest g with g^dim >= n)      */
     int32_t search_res;       /* search-grid cells per axis used this step                      */
-    int32_t n_rho;            /* with rho_audit: #{i : 2 delta_i > c_i}, delta_i = |p'_i - p_i|
+    int32_t n_rho;            /* CERT_AUDIT_RHO: #{i : 2 delta_i > c_i}, delta_i = |p'_i - p_i|
                                  and c_i the pre-step clearance, both FP32 (the heuristic
                                  rho_i > 1/2 of Sec. 3 and Table 1; a guess, not a bound)     */
-    int32_t n_rho_hit;        /* with rho_audit: flagged points whose nn changed; recall =
+    int32_t n_rho_hit;        /* CERT_AUDIT_RHO: flagged points whose nn changed; recall =
                                  n_rho_hit / n_failed, false = (n_rho - n_rho_hit) / n_rho      */
+    double gyration;          /* CERT_AUDIT_GEOMETRY: radius of gyration of the failed points'
+                                 post-step positions, sqrt(mean |p'_i - centroid|^2); 0 with
+                                 fewer than two failures.  FP64 sums in any order: within
+                                 1e-5 of the two-pass value                                   */
+    double compactness;       /* CERT_AUDIT_GEOMETRY: 1 - gyration / (the same radius over all
+                                 points of the scene), clamped to [0, 1]: 1 when the failures
+                                 collapse to a point, near 0 when they spread like the scene;
+                                 1 for a single failure, 0 without failures                   */
 } cert_scene_result;
 
 /* Device views of the per-point results; valid until the next call that

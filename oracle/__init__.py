@@ -17,6 +17,10 @@ Nearest-Neighbour Structures"):
   (+ guard), the remark closing Sec. 5; ``disp`` gives delta_i.
 * ``rho`` -- the local heuristic rho_i = delta_i / c_i > 1/2 of Sec. 3 and
   Table 1 (recall and false-flag audit; not a bound).
+* ``gyration`` / ``compactness`` -- the failures' spatial spread, the
+  frontier descriptors of the paper's transition log (Sec. 6 dataset columns,
+  named there but not defined; read as the radius of gyration of the failed
+  points and one minus its ratio to the scene's).
 * ``ClockState`` -- the cumulative clock of the per-step cost subsection
   (Thm A.3): a certificate last revisited at clock S_i with clearance c^rev_i
   stays valid while 4 (S - S_i) < c^rev_i.
@@ -299,6 +303,8 @@ class StepResult:
     rho: np.ndarray               # bool: flagged by the local heuristic rho_i > 1/2
     n_rho: int                    # flagged points
     n_rho_hit: int                # flagged points that failed
+    gyration: float               # radius of gyration of the failed points (post-step)
+    compactness: float            # 1 - gyration / (the scene's radius), in [0, 1]
 
 
 def clearances(cert: Certificates) -> np.ndarray:
@@ -339,7 +345,34 @@ def step(p_old, p_new, cert_old: Certificates, nthreads: int = 0, rule: str = "s
         eps_t=e, frontier=F, cert=new, failed=failed, cell=cell, g_h=g, H=H, H_cand=Hc,
         m=m, m_cand=mc, C=C, n_failed=int(failed.sum()),
         n_missed=int((failed & ~inF).sum()), n_false=int((inF & ~failed).sum()),
-        med_c=trunc_median(clearances(cert_old)), **_rho_audit(cert_old, delta, failed))
+        med_c=trunc_median(clearances(cert_old)), **_rho_audit(cert_old, delta, failed),
+        **_geometry(p_new, failed))
+
+
+def gyration(points) -> float:
+    """Radius of gyration sqrt(mean |p - centroid|^2) of float32 points, in FP64
+    (two passes: the centroid, then the mean squared distance to it); 0 for
+    fewer than two points."""
+    q = np.asarray(points, dtype=np.float64)
+    if q.shape[0] < 2:
+        return 0.0
+    c = q.mean(axis=0)
+    return float(np.sqrt(((q - c) ** 2).sum(axis=1).mean()))
+
+
+def compactness(failed_points, all_points) -> float:
+    """1 - gyration(failures) / gyration(scene), clamped to [0, 1]; 1 for a
+    single failure (or a scene of one position), 0 without failures."""
+    if len(failed_points) == 0:
+        return 0.0
+    g_all = gyration(all_points)
+    if g_all <= 0.0:
+        return 1.0
+    return float(min(1.0, max(0.0, 1.0 - gyration(failed_points) / g_all)))
+
+
+def _geometry(p_new: np.ndarray, failed: np.ndarray) -> dict:
+    return {"gyration": gyration(p_new[failed]), "compactness": compactness(p_new[failed], p_new)}
 
 
 def _rho_audit(cert_old: Certificates, delta: np.ndarray, failed: np.ndarray) -> dict:

@@ -30,7 +30,7 @@ class cert_config(ctypes.Structure):
                 ("offsets", ctypes.POINTER(ctypes.c_int64)), ("n_total", ctypes.c_int64),
                 ("cell_scale", ctypes.c_float), ("policy", ctypes.c_int32),
                 ("bucket_factor", ctypes.c_int32), ("cell_quantile", ctypes.c_float),
-                ("frontier_rule", ctypes.c_int32), ("rho_audit", ctypes.c_int32)]
+                ("frontier_rule", ctypes.c_int32), ("audit", ctypes.c_int32)]
 
 
 class cert_scene_result(ctypes.Structure):
@@ -42,7 +42,8 @@ class cert_scene_result(ctypes.Structure):
                 ("frontier_cells", ctypes.c_int32), ("occupied_cells", ctypes.c_int32),
                 ("strategy", ctypes.c_int32), ("pred_inc", ctypes.c_float), ("pred_reb", ctypes.c_float),
                 ("grid_res", ctypes.c_int32), ("search_res", ctypes.c_int32),
-                ("n_rho", ctypes.c_int32), ("n_rho_hit", ctypes.c_int32)]
+                ("n_rho", ctypes.c_int32), ("n_rho_hit", ctypes.c_int32), ("gyration", ctypes.c_double),
+                ("compactness", ctypes.c_double)]
 
 
 SCENE_DTYPE = np.dtype([(n, np.dtype(t).newbyteorder("=")) for n, t in [
@@ -51,7 +52,8 @@ SCENE_DTYPE = np.dtype([(n, np.dtype(t).newbyteorder("=")) for n, t in [
     ("n_missed", np.int32), ("n_false", np.int32), ("n_searched", np.int32),
     ("failed_cells", np.int32), ("frontier_cells", np.int32), ("occupied_cells", np.int32),
     ("strategy", np.int32), ("pred_inc", np.float32), ("pred_reb", np.float32),
-    ("grid_res", np.int32), ("search_res", np.int32), ("n_rho", np.int32), ("n_rho_hit", np.int32)]])
+    ("grid_res", np.int32), ("search_res", np.int32), ("n_rho", np.int32), ("n_rho_hit", np.int32),
+    ("gyration", np.float64), ("compactness", np.float64)]])
 assert SCENE_DTYPE.itemsize == ctypes.sizeof(cert_scene_result)
 
 
@@ -304,6 +306,18 @@ def cert_mlp_adam(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e
                                float(beta2), float(eps), _stream_ptr(stream)))
 
 
+AUDIT = {"rho": 1, "geometry": 2}    # cert_audit
+
+
+def audit_flags(audit) -> int:
+    """cert_audit flags from an int or names ("rho", "geometry")."""
+    if isinstance(audit, (int, np.integer)):
+        return int(audit)
+    if isinstance(audit, str):
+        audit = (audit,)
+    return sum(AUDIT[a] for a in set(audit))
+
+
 class Context:
     """A batch of scenes whose certificates are maintained on the GPU.
 
@@ -313,7 +327,7 @@ class Context:
     """
 
     def __init__(self, pos, offsets=None, cell_scale=0.0, policy=CERT_INCREMENTAL, stream=None,
-                 bucket_factor=0, cell_quantile=0.0, frontier_rule="step", rho_audit=False):
+                 bucket_factor=0, cell_quantile=0.0, frontier_rule="step", audit=()):
         import torch
         self.dim = int(pos.shape[1])
         self._keep = []
@@ -331,7 +345,7 @@ class Context:
         cfg.bucket_factor = int(bucket_factor)
         cfg.cell_quantile = float(cell_quantile)
         cfg.frontier_rule = FRONTIER_RULE[frontier_rule] if isinstance(frontier_rule, str) else int(frontier_rule)
-        cfg.rho_audit = 1 if rho_audit else 0
+        cfg.audit = audit_flags(audit)
         self.n_scenes = cfg.n_scenes
         self.n = cfg.n_total
         h = ctypes.c_void_p()

@@ -25,7 +25,7 @@ struct cert_ctx {
     int bucket_factor = 1;
     int policy = STRAT_INC;
     int frontier_rule = CERT_FRONTIER_STEP;
-    int rho_audit = 0;
+    int audit = 0;
     double *clk_s = nullptr;       // cumulative-clock rule: S_i, c^rev_i, (d1 + d2)^rev_i per point
     float *clk_c = nullptr, *clk_g = nullptr;
     std::vector<SceneParams> h_sp;
@@ -198,7 +198,7 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.res = c->res;
     a.policy = c->policy;
     a.frontier_rule = c->frontier_rule;
-    a.rho_audit = c->rho_audit;
+    a.audit = c->audit;
     a.clk_s = c->clk_s;
     a.clk_c = c->clk_c;
     a.clk_g = c->clk_g;
@@ -245,7 +245,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     if (!d_pos) return fail(nullptr, CERT_EINVAL, "positions are NULL");
     if (cfg->dim != 2 && cfg->dim != 3) return fail(nullptr, CERT_EINVAL, "dim must be 2 or 3");
     if (cfg->n_scenes < 1) return fail(nullptr, CERT_EINVAL, "n_scenes must be >= 1");
-    if (cfg->rho_audit != 0 && cfg->rho_audit != 1) return fail(nullptr, CERT_EINVAL, "rho_audit must be 0 or 1");
+    if (cfg->audit & ~(CERT_AUDIT_RHO | CERT_AUDIT_GEOMETRY)) return fail(nullptr, CERT_EINVAL, "unknown audit flag");
     if (cfg->frontier_rule < CERT_FRONTIER_STEP || cfg->frontier_rule > CERT_FRONTIER_CLOCK)
         return fail(nullptr, CERT_EINVAL, "unknown frontier_rule");
     if (cfg->bucket_factor != 0 && cfg->bucket_factor != 1 && cfg->bucket_factor != 2 && cfg->bucket_factor != 4 &&
@@ -278,7 +278,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->bucket_factor = cfg->bucket_factor > 0 ? cfg->bucket_factor : 1;
     c->policy = cfg->policy == STRAT_AUTO ? STRAT_INC : cfg->policy;
     c->frontier_rule = cfg->frontier_rule;
-    c->rho_audit = cfg->rho_audit;
+    c->audit = cfg->audit;
     cudaStream_t s = (cudaStream_t)stream;
 
     // ---- per-scene layout

@@ -66,6 +66,8 @@ struct SceneAcc {
     int32_t pad;
     double s_fail;                 // sum over cells of n ln n, failures
     double s_front;                // sum over cells of n ln n, detected frontier
+    double f_sum[4];               // geometry audit: sums of x, y, z, |p|^2 over the failures
+    double a_sum[4];               // ... and over every point of the scene
 };
 
 struct Top3 {

@@ -39,14 +39,14 @@ struct StepArgs {
     int32_t *far_count;            // number of entries in far_list (zeroed every call)
     // certificates
     int frontier_rule;             // cert_frontier_rule
-    int rho_audit;                 // 1: flag 2 delta_i > c_i in inF bit 1 and count it
+    int audit;                     // cert_audit flags: rho (inF bit 1), geometry (position sums)
     double *clk_s;                 // clock rule, per point: clock of the last revisit
     float *clk_c, *clk_g;          // ... and c, d1 + d2 of the certificate then
     int32_t *nn, *nn2, *nn3;       // nearest, runner-up, third stored candidate (-1: none)
     float *d1sq, *d2sq, *L;        // L: lower bound on the distance to every other point
     // step outputs
     int32_t *hcell, *hocc, *hfail, *hcand;
-    uint8_t *inF, *failed;         // inF bit 0: in F_t; bit 1: rho-flagged (rho_audit)
+    uint8_t *inF, *failed;         // inF bit 0: in F_t; bit 1: rho-flagged (CERT_AUDIT_RHO)
     int32_t *frontier, *fstart;
     // chained-scan state
     uint64_t *tstat_b, *tstat_p;

@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
             // the local heuristic of Sec. 3: rho_i = delta_i / c_i > 1/2, taken as
             // 2 delta_i > c_i on the FP32 values (exact: the doubling rounds nothing)
             uint32_t r = 0u;
-            if (a.rho_audit) {
+            if (a.audit & CERT_AUDIT_RHO) {
                 r = (__fmul_rn(2.0f, __fsqrt_rn(a.pos_new[i].w)) > c) ? 1u : 0u;
                 rho |= r << k;
             }
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     const unsigned m = scene_run_mask(cur);
     const int fc = run_sum_i32(m, acc_first);
     const double sd = run_sum_f64(m, acc_dl);
-    const int nr = a.rho_audit ? run_sum_i32(m, acc_rho) : 0;
+    const int nr = (a.audit & CERT_AUDIT_RHO) ? run_sum_i32(m, acc_rho) : 0;
     if (cur >= 0 && run_leader(m)) {
         if (fc) atomicAdd(&a.acc[cur].frontier_cells, fc);
         if (sd != 0.0) atomicAdd(&a.acc[cur].s_front, sd);
@@ -1108,6 +1108,52 @@ __global__ void __launch_bounds__(kThreads) k_far(const StepArgs a)
     }
 }
 
+// ============================================================================ k_geometry
+
+// CERT_AUDIT_GEOMETRY only (launched when the flag is set): per scene, the
+// FP64 sums of x, y, z and |p|^2 of the post-step positions of every point
+// and of the failed points, for the radius of gyration in k_finalize.  Kept
+// out of the repair kernels, which it would cost registers.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_geometry(const StepArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int s = -1;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool f = false;
+    if (i < a.n_total) {
+        s = a.scene_of[i];
+        p = a.pos_new[i];
+        f = a.failed[i] != 0;
+    }
+    const double x = p.x, y = p.y, z = (DIM == 3) ? (double)p.z : 0.0;
+    const double q = x * x + y * y + z * z;
+    const unsigned m = scene_run_mask(s);
+    const double v[4] = {x, y, z, q};
+    double all[4], fail[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        all[k] = run_sum_f64(m, v[k]);
+        fail[k] = run_sum_f64(m, f ? v[k] : 0.0);
+    }
+    if (s >= 0 && run_leader(m)) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            atomicAdd(&a.acc[s].a_sum[k], all[k]);
+            if (fail[k] != 0.0) atomicAdd(&a.acc[s].f_sum[k], fail[k]);
+        }
+    }
+}
+
+// sqrt(mean |p|^2 - |mean p|^2) from the FP64 sums of x, y, z, |p|^2 of n points
+__device__ __forceinline__ double gyration_radius(const double *sum, int n)
+{
+    if (n < 2) return 0.0;
+    const double inv = 1.0 / (double)n;
+    const double mx = sum[0] * inv, my = sum[1] * inv, mz = sum[2] * inv;
+    return sqrt(fmax(0.0, sum[3] * inv - (mx * mx + my * my + mz * mz)));
+}
+
 // ============================================================================ k_finalize
 
 __device__ __forceinline__ double norm_entropy(int n, double s_nlogn, int C)
@@ -1148,6 +1194,13 @@ __global__ void k_finalize(const StepArgs a)
         r.search_res = st.g_cur;
         r.n_rho = acc.n_rho;
         r.n_rho_hit = acc.n_rho_hit;
+        r.gyration = 0.0;
+        r.compactness = 0.0;
+        if ((a.audit & CERT_AUDIT_GEOMETRY) && acc.n_failed > 0) {
+            r.gyration = gyration_radius(acc.f_sum, acc.n_failed);
+            const double all = gyration_radius(acc.a_sum, sp.n);
+            r.compactness = all > 0.0 ? fmin(1.0, fmax(0.0, 1.0 - r.gyration / all)) : 1.0;
+        }
         a.res[s] = r;
         if (r.eps_t > __fmul_ru(a.declared_eps, 1.0f + 0x1p-20f)) atomicOr(a.status, ST_EBOUND);
         st.prev_fail_ratio = (float)acc.n_failed / (float)max(1, nF);
@@ -1186,7 +1239,11 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
         k_search<DIM><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
         if (cudaPeekAtLastError() == cudaSuccess) k_far<DIM><<<kFarCtas, kThreads, 0, st>>>(a);
         break;
-    case PH_FINALIZE: k_finalize<<<nblk(a.n_scenes, 128), 128, 0, st>>>(a); break;
+    case PH_FINALIZE:
+        if (a.mode == MODE_STEP && (a.audit & CERT_AUDIT_GEOMETRY))
+            k_geometry<DIM><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(a);
+        if (cudaPeekAtLastError() == cudaSuccess) k_finalize<<<nblk(a.n_scenes, 128), 128, 0, st>>>(a);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

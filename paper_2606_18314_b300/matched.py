@@ -13,7 +13,8 @@ This module runs that experiment on this library:
 
 * ``survey`` steps one seeded scene of a family through the GPU path and
   records the per-transition counts (failures, H, the cells m they meet, the
-  detected frontier and the cells it meets);
+  detected frontier and the cells it meets) and the failures' gyration and
+  compactness;
 * ``select`` picks, as the paper does, the pair whose failure counts agree
   within the tolerance and whose entropies differ most;
 * ``time_transition`` replays one transition back and forth (the failing set
@@ -48,7 +49,7 @@ def survey(cert, family, n, dim, eps, steps, seed=1, horizon=None):
     horizon = horizon or max(steps, 64)
     fr = scenes.Motion(family, n, dim, eps, seed=seed, steps=horizon).frames(steps)
     dev = torch.from_numpy(fr).cuda()
-    ctx = cert.Context(dev[0])
+    ctx = cert.Context(dev[0], audit="geometry")
     rows = []
     try:
         for t in range(steps):
@@ -58,7 +59,8 @@ def survey(cert, family, n, dim, eps, steps, seed=1, horizon=None):
             rows.append({"family": family, "eps": eps, "t": t, "n_failed": int(r["n_failed"]),
                          "H": float(r["H"]), "m": int(r["failed_cells"]), "C": int(r["occupied_cells"]),
                          "n_frontier": int(r["n_frontier"]), "frontier_cells": int(r["frontier_cells"]),
-                         "n_searched": int(r["n_searched"]), "n_missed": int(r["n_missed"])})
+                         "n_searched": int(r["n_searched"]), "n_missed": int(r["n_missed"]),
+                         "gyration": float(r["gyration"]), "compactness": float(r["compactness"])})
     finally:
         ctx.close()
     return fr, rows

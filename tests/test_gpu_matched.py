@@ -31,7 +31,8 @@ def oracle_rows(frames, family, eps):
         r = oracle.step(frames[t], frames[t + 1], c)
         c = r.cert
         rows.append({"family": family, "eps": eps, "t": t, "n_failed": r.n_failed, "H": r.H, "m": r.m,
-                     "C": r.C, "n_frontier": len(r.frontier), "frontier_cells": r.m_cand})
+                     "C": r.C, "n_frontier": len(r.frontier), "frontier_cells": r.m_cand,
+                     "gyration": r.gyration, "compactness": r.compactness})
     return rows
 
 
@@ -48,6 +49,7 @@ def test_survey_and_selection_match_the_oracle(cert):
         for k in ("n_failed", "m", "C", "n_frontier", "frontier_cells"):
             assert g[k] == o[k], (tag, k, g[k], o[k])
         assert abs(g["H"] - o["H"]) <= 1e-6, tag
+        assert abs(g["gyration"] - o["gyration"]) <= 1e-5 and abs(g["compactness"] - o["compactness"]) <= 1e-5, tag
         assert g["n_missed"] == 0, tag
     pg, po = matched.select(ga, gb), matched.select(oa, ob)
     assert pg is not None and po is not None

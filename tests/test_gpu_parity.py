@@ -12,6 +12,10 @@ from paper_2606_18314_b300 import scenes
 pytestmark = pytest.mark.gpu
 
 H_TOL = 1e-6
+# gyration from one-pass FP64 sums (any order) against the oracle's two passes:
+# the variance's cancellation error is at most n u sum|p|^2 ~ 1e-11 here, so
+# the radius differs by at most sqrt of that
+GEOM_TOL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -195,16 +199,18 @@ def test_frontier_rules_match_oracle(torch, rule, family):
 
 
 @pytest.mark.parametrize("rule", ["step", "point", "clock"])
-def test_rho_audit_matches_oracle(torch, rule):
-    """rho_audit: the flagged count (k_scan) and the flagged failures (counted
-    by the refresh, the search, the far pass and the all-pairs merge) equal the
-    oracle's in every scene of a batch, under every frontier rule and strategy;
-    without the audit both counts stay 0 and nothing else changes."""
+def test_audits_match_oracle(torch, rule):
+    """The audits: the rho heuristic's flagged count (k_scan) and flagged
+    failures (counted by the refresh, the search, the far pass and the
+    all-pairs merge) equal the oracle's, and the failures' gyration and
+    compactness (k_geometry, FP64 sums in any order) are within 1e-5 of its
+    two-pass values, in every scene of a batch, under every frontier rule and
+    strategy; without the audits those fields stay 0 and nothing else changes."""
     from paper_2606_18314_b300 import cert
     m = scenes.BatchMotion.mixed(n_scenes=10, lo=300, hi=3000, eps=2e-3, seed=21)
     off = m.offsets
     frames = m.frames(6)
-    ctx = cert.Context(dev(torch, frames[0]), offsets=off, frontier_rule=rule, rho_audit=True)
+    ctx = cert.Context(dev(torch, frames[0]), offsets=off, frontier_rule=rule, audit=("rho", "geometry"))
     plain = cert.Context(dev(torch, frames[0]), offsets=off, frontier_rule=rule)
     refs = [oracle.top2(frames[0][off[s]:off[s + 1]]) for s in range(10)]
     clocks = [oracle.ClockState(r) for r in refs] if rule == "clock" else [None] * 10
@@ -223,9 +229,13 @@ def test_rho_audit_matches_oracle(torch, rule):
             assert_step_equal(ctx, res, views, r, s=s, tag=tag)
             assert int(res[s]["n_rho"]) == r.n_rho, (tag, int(res[s]["n_rho"]), r.n_rho)
             assert int(res[s]["n_rho_hit"]) == r.n_rho_hit, (tag, int(res[s]["n_rho_hit"]), r.n_rho_hit)
+            assert abs(float(res[s]["gyration"]) - r.gyration) <= GEOM_TOL, (tag, float(res[s]["gyration"]), r.gyration)
+            assert abs(float(res[s]["compactness"]) - r.compactness) <= GEOM_TOL, (tag, float(res[s]["compactness"]),
+                                                                                  r.compactness)
             seen_hits += r.n_rho_hit
             refs[s] = r.cert
         assert np.all(res0["n_rho"] == 0) and np.all(res0["n_rho_hit"] == 0)
+        assert np.all(res0["gyration"] == 0) and np.all(res0["compactness"] == 0)
         for k in ("n_frontier", "n_failed", "n_missed", "n_false", "failed_cells", "frontier_cells"):
             assert np.array_equal(res0[k], res[k]), k
     assert seen_hits > 0
