@@ -194,15 +194,18 @@ cert_status cert_step_host(cert_ctx *ctx, const float *h_pos_new, float eps, int
  * memory returns only when the step is done, which stops the overlap.
  * Frame k+1 is copied on the context's own copy stream,
  * into the other of two device staging buffers, while step k runs on
- * `stream`; each step then copies its per-scene scalars to
- * h_scenes[k * n_scenes ...] (may be NULL).  Results equal n_steps calls of
- * cert_step_host.  Each step is replayed from a CUDA graph of cert_step,
- * captured on first use for each parity of the position and staging buffers
- * and captured again when eps, the strategy or a setting that the step reads
- * (cell scale, cell quantile, selector) changes; with phase profiling on, the
- * steps are launched directly.  Synchronises `stream` before returning.
- * Creates the copy and capture streams and the events on first use;
- * allocates no device memory.  Errors:
+ * `stream`.  Step k writes its per-scene scalars into one of two device
+ * result slots, and a second copy stream moves them to
+ * h_scenes[k * n_scenes ...] (may be NULL) while step k+1 runs; after the
+ * last step they are also where cert_sync_result and the views read them.
+ * Results equal n_steps calls of cert_step_host.  Each step is replayed from
+ * a CUDA graph of cert_step, captured on first use for each parity of the
+ * position and staging buffers and captured again when eps, the strategy or
+ * a setting that the step reads (cell scale, cell quantile, selector)
+ * changes; with phase profiling on, the steps are launched directly.
+ * Synchronises `stream` and the copy streams before returning.  Creates the
+ * copy and capture streams and the events on first use; allocates no device
+ * memory.  Errors:
  * CERT_EINVAL for a NULL table or frame, or n_steps < 0; CERT_ECUDA for a
  * failed copy or launch. */
 cert_status cert_step_host_stream(cert_ctx *ctx, const float *const *h_frames, int32_t n_steps, float eps,

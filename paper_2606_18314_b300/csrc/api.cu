@@ -61,9 +61,14 @@ struct cert_ctx {
     float *feat = nullptr;          // [S][8] selector features of the last step
     // snapshot of the mutable state (allocated by the first cert_snapshot)
     char *snap = nullptr;
-    // pipelined host steps: a second staging buffer, a copy stream and events (created on first use)
+    // pipelined host steps: a second staging buffer, a copy stream and events (created on first use);
+    // each buffer parity's steps write their scalars to their own slot of res_ring, which a second
+    // copy stream moves to the host while the next step runs
     float *stage2 = nullptr;
-    cudaStream_t copy_stream = nullptr;
+    cudaStream_t copy_stream = nullptr, d2h_stream = nullptr;
+    cert_scene_result *res_ring = nullptr;    // [2][S]
+    cert_scene_result *res_target = nullptr;  // where k_finalize writes (nullptr: res)
+    cudaEvent_t ev_d2h[2] = {nullptr, nullptr};
     // one-step CUDA graphs replayed by the pipelined host steps, one per
     // (position buffer, staging buffer) parity; rebuilt when eps, the strategy
     // or a setting baked into the step arguments changes
@@ -195,7 +200,7 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.ntiles_b = c->ntiles_b;
     a.ntiles_p = 0;
     a.nlogn = c->nlogn;
-    a.res = c->res;
+    a.res = c->res_target ? c->res_target : c->res;
     a.policy = c->policy;
     a.frontier_rule = c->frontier_rule;
     a.audit = c->audit;
@@ -336,7 +341,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_nlogn = cv.take<double>(kNlognTable),
                  o_stage = cv.take<float>(N * c->dim), o_stage2 = cv.take<float>(N * c->dim), o_items = cv.take<APItem>(items.size()),
                  o_pd = cv.take<float>(3 * apoff), o_pj = cv.take<int32_t>(3 * apoff),
-                 o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16), o_feat = cv.take<float>(S * 8);
+                 o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16), o_feat = cv.take<float>(S * 8),
+                 o_resring = cv.take<cert_scene_result>(2 * S);
     const int64_t Nclk = (c->frontier_rule == CERT_FRONTIER_CLOCK) ? N : 0;
     const size_t o_clks = cv.take<double>(Nclk), o_clkc = cv.take<float>(Nclk), o_clkg = cv.take<float>(Nclk);
     cv.off = (cv.off + 255) & ~size_t(255);
@@ -381,6 +387,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->nlogn = (double *)(b + o_nlogn);
     c->stage = (float *)(b + o_stage);
     c->stage2 = (float *)(b + o_stage2);
+    c->res_ring = (cert_scene_result *)(b + o_resring);
     c->ap_items = (APItem *)(b + o_items);
     c->ap_pd = (float *)(b + o_pd);
     c->ap_pj = (int32_t *)(b + o_pj);
@@ -545,7 +552,9 @@ static cert_status step_by_graph(cert_ctx *c, const float *stage, int b, float e
         const cudaStream_t last0 = c->last;
         const bool stepped0 = c->stepped;
         CK(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+        c->res_target = c->res_ring + (size_t)b * c->S;   // this parity's result slot
         const cert_status rc = cert_step(c, stage, eps, strategy, nullptr, c->capture_stream);
+        c->res_target = nullptr;
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(c->capture_stream, &graph);
         c->cur = cur0;              // the capture enqueued nothing: undo its bookkeeping
@@ -581,15 +590,21 @@ cert_status cert_step_host_stream(cert_ctx *c, const float *const *h_frames, int
     const int64_t frame = c->N * c->dim;
     if (!c->copy_stream) {
         CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        CK(c, cudaStreamCreateWithFlags(&c->d2h_stream, cudaStreamNonBlocking));
         for (int k = 0; k < 2; ++k) {
             CK(c, cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
             CK(c, cudaEventCreateWithFlags(&c->ev_used[k], cudaEventDisableTiming));
+            CK(c, cudaEventCreateWithFlags(&c->ev_d2h[k], cudaEventDisableTiming));
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
     float *buf[2] = {c->stage, c->stage2};
-    // both buffers are free once the caller's stream has reached this point
-    for (int k = 0; k < 2; ++k) CK(c, cudaEventRecord(c->ev_used[k], s));
+    const size_t res_bytes = size_t(c->S) * sizeof(cert_scene_result);
+    // both buffers and both result slots are free once the caller's stream has reached this point
+    for (int k = 0; k < 2; ++k) {
+        CK(c, cudaEventRecord(c->ev_used[k], s));
+        CK(c, cudaEventRecord(c->ev_d2h[k], s));
+    }
     for (int32_t k = 0; k < n_steps; ++k) {
         const int b = k & 1;
         // copy frame k while step k-1 runs; buffer b was last read by step k-2
@@ -598,15 +613,33 @@ cert_status cert_step_host_stream(cert_ctx *c, const float *const *h_frames, int
                               cudaMemcpyHostToDevice, c->copy_stream));
         CK(c, cudaEventRecord(c->ev_copied[b], c->copy_stream));
         CK(c, cudaStreamWaitEvent(s, c->ev_copied[b], 0));
-        // replayed as a graph (fewer launch gaps) unless phase profiling is on
-        const cert_status rc = c->prof_on ? cert_step(c, buf[b], eps, strategy, nullptr, stream)
-                                          : step_by_graph(c, buf[b], b, eps, strategy, s);
+        // result slot b was last read back for step k-2 (long done by now)
+        CK(c, cudaStreamWaitEvent(s, c->ev_d2h[b], 0));
+        // replayed as a graph (fewer launch gaps) unless phase profiling is on; either
+        // way step k's scalars land in result slot b
+        cert_status rc;
+        if (c->prof_on) {
+            c->res_target = c->res_ring + (size_t)b * c->S;
+            rc = cert_step(c, buf[b], eps, strategy, nullptr, stream);
+            c->res_target = nullptr;
+        } else {
+            rc = step_by_graph(c, buf[b], b, eps, strategy, s);
+        }
         if (rc != CERT_OK) return rc;
         CK(c, cudaEventRecord(c->ev_used[b], s));
-        if (h_scenes)
-            CK(c, cudaMemcpyAsync(h_scenes + (size_t)k * c->S, c->res, size_t(c->S) * sizeof(cert_scene_result),
-                                  cudaMemcpyDeviceToHost, s));
+        // the read-back waits for step k on its own stream, so step k+1 starts at once
+        if (h_scenes) {
+            CK(c, cudaStreamWaitEvent(c->d2h_stream, c->ev_used[b], 0));
+            CK(c, cudaMemcpyAsync(h_scenes + (size_t)k * c->S, c->res_ring + (size_t)b * c->S, res_bytes,
+                                  cudaMemcpyDeviceToHost, c->d2h_stream));
+            CK(c, cudaEventRecord(c->ev_d2h[b], c->d2h_stream));
+        }
     }
+    // the last step's scalars also where cert_sync_result and the views read them
+    if (n_steps > 0)
+        CK(c, cudaMemcpyAsync(c->res, c->res_ring + (size_t)((n_steps - 1) & 1) * c->S, res_bytes,
+                              cudaMemcpyDeviceToDevice, s));
+    CK(c, cudaStreamSynchronize(c->d2h_stream));
     CK(c, cudaStreamSynchronize(s));
     return CERT_OK;
 }
@@ -848,8 +881,10 @@ void cert_destroy(cert_ctx *c)
     for (int k = 0; k < 2; ++k) {
         if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
         if (c->ev_used[k]) cudaEventDestroy(c->ev_used[k]);
+        if (c->ev_d2h[k]) cudaEventDestroy(c->ev_d2h[k]);
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->d2h_stream) cudaStreamDestroy(c->d2h_stream);
     for (auto &g : c->step_graph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
