@@ -170,10 +170,11 @@ def cycle_index(k, F):
     return r + 1 if r < F else 2 * F - r - 1
 
 
-def cpu_baseline(frames, offsets, dim, budget_s, per_step_budget=None, steps_exact=None):
+def cpu_baseline(frames, offsets, dim, budget_s, per_step_budget=None, steps_exact=None, warmup=0):
     """The oracle as it stands on this host's cores over a bounded sample:
     whole scenes in a seeded random order (as many as fit the per-step budget,
-    at least one), stepped through the same frames."""
+    at least one), stepped through the same frames; ``warmup`` untimed steps
+    first."""
     import oracle
     S = len(offsets) - 1
     sizes = np.diff(offsets)
@@ -189,11 +190,17 @@ def cpu_baseline(frames, offsets, dim, budget_s, per_step_budget=None, steps_exa
         chosen.append(int(s))
         cost += c
     certs = {s: oracle.top2(frames[0][offsets[s]:offsets[s + 1]]) for s in chosen}
-    pts, steps, t0 = 0, 0, time.perf_counter()
     F = frames.shape[0] - 1
     prev = 0
+    for w in range(warmup):
+        k = cycle_index(w, F)
+        for s in chosen:
+            r = oracle.step(frames[prev][offsets[s]:offsets[s + 1]], frames[k][offsets[s]:offsets[s + 1]], certs[s])
+            certs[s] = r.cert
+        prev = k
+    pts, steps, t0 = 0, 0, time.perf_counter()
     while True:
-        k = cycle_index(steps, F)
+        k = cycle_index(steps + warmup, F)
         for s in chosen:
             a, b = frames[prev][offsets[s]:offsets[s + 1]], frames[k][offsets[s]:offsets[s + 1]]
             r = oracle.step(a, b, certs[s])
@@ -219,11 +226,12 @@ def run_reference(args, rank, world):
     dim = frames.shape[2]
     per_step = max(0.02, 120.0 / max(1, args.steps + args.warmup))
     cb, steps, el = cpu_baseline(frames, offsets, dim, budget_s=per_step * args.steps, per_step_budget=per_step,
-                                 steps_exact=max(1, args.steps))
+                                 steps_exact=max(1, args.steps), warmup=max(0, args.warmup))
     cfg = dict(cfg)
     cfg["l2"] = "host oracle (no GPU)"
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": 1,
-            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * el / max(1, steps), "higher_is_better": True,
+            "steps": steps, "warmup": max(0, args.warmup), "ms_per_step": 1e3 * el / max(1, steps),
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
