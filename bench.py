@@ -376,7 +376,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--clocks-out", default=None, help="keep the nvidia-smi clock samples here ({rank} expands)")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--prof-steps", type=int, default=200)
     ap.add_argument("--regret-steps", type=int, default=32)
     ap.add_argument("--rule-steps", type=int, default=32, help="steps per frontier rule in the detection report")
