@@ -332,6 +332,35 @@ __global__ void k_pack(const float *pos, int n, float4 *out, uint32_t *status)
     out[i] = p;
 }
 
+// j-chunks for one point set of n candidates: the count that minimises the
+// time of the grid, modelled as (waves of resident CTAs) x (chunk length +
+// a fixed cost of kApChunkFixed candidates per CTA); ties go to fewer chunks
+// (a smaller merge).
+int allpairs_chunks_for(long long qblocks, long long n, int dim, int cap)
+{
+    constexpr long long kApChunkFixed = 256;
+    int dev = 0, sms = 1, bps = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        sms = 148;
+    const cudaError_t e = (dim == 3) ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_allpairs<3>, kApThreads, 0)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_allpairs<2>, kApThreads, 0);
+    if (e != cudaSuccess || bps < 1) bps = 1;
+    const long long wave = (long long)sms * bps;
+    cap = std::max(1, std::min(cap, 64));
+    int best = 1;
+    long long best_cost = -1;
+    for (int nch = 1; nch <= cap; ++nch) {
+        const long long waves = (qblocks * nch + wave - 1) / wave;
+        const long long cost = waves * ((n + nch - 1) / nch + kApChunkFixed);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = nch;
+        }
+    }
+    return best;
+}
+
 int allpairs_chunks(long long qblocks, int dim, int cap)
 {
     // j-chunks per query block so that the grid fills whole waves of resident

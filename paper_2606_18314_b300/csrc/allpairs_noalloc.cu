@@ -87,7 +87,7 @@ extern "C" cert_status cert_allpairs_noalloc(const float *d_pos, int64_t n, int3
     const int64_t nqb = (nq + kApQBlock - 1) / kApQBlock;
     const int64_t room = (int64_t)kNoAllocScratchBytes - (int64_t)align256(size_t(n) * sizeof(float4)) - 4096;
     const int64_t fit = room > 0 ? room / (nq * int64_t(6 * sizeof(float))) : 1;
-    const int64_t nch = allpairs_chunks(nqb, dim, (int)std::max<int64_t>(
+    const int64_t nch = allpairs_chunks_for(nqb, n, dim, (int)std::max<int64_t>(
                                                       1, std::min<int64_t>({fit, (n + 255) / 256, int64_t(64)})));
     const long long P = (long long)nq * nch;
     const size_t o_pos = 0;

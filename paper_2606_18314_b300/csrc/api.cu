@@ -957,7 +957,7 @@ extern "C" cert_status cert_allpairs(const float *d_pos, int64_t n, int32_t dim,
     if (nq == 0) return CERT_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int nqb = (int)ceil_div(nq, kApQBlock);
-    const int nch = allpairs_chunks(nqb, dim, (int)std::min<int64_t>(64, ceil_div(n, 256)));
+    const int nch = allpairs_chunks_for(nqb, n, dim, (int)std::min<int64_t>(64, ceil_div(n, 256)));
     SceneParams p;
     std::memset(&p, 0, sizeof(p));
     p.pt_off = 0;

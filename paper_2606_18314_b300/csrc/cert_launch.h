@@ -106,6 +106,7 @@ constexpr int kApTile = 2048;                  // candidates staged per shared-m
 cudaError_t launch_allpairs(const APArgs &a, cudaStream_t st);
 // j-chunks per query block that fill whole waves of resident k_allpairs CTAs (1 <= result <= cap).
 int allpairs_chunks(long long qblocks, int dim, int cap);
+int allpairs_chunks_for(long long qblocks, long long n, int dim, int cap);
 cudaError_t launch_allpairs_merge(const APArgs &a, const APMergeOut &o, long long n_queries_total,
                                   cudaStream_t st);
 cudaError_t launch_pack(const float *pos, int n, int dim, float4 *out, uint32_t *status, cudaStream_t st);
