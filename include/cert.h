@@ -325,8 +325,8 @@ cert_status cert_profile_end(cert_ctx *ctx, float *h_ms, int32_t max_steps, int3
  * Same arguments, same results (bit for bit) as cert_allpairs.
  *   - Scratch is one file-scope device array of 32 MiB, held by every GPU that
  *     loads the library until the process exits.  A call needs about
- *     16 n + 24 nq k bytes (k = number of j-chunks, 1 to 64, chosen to fill
- *     whole waves of CTAs within the array); every call with
+ *     16 n + 24 nq k bytes (k = number of j-chunks, 1 to 64, chosen as in
+ *     cert_allpairs but no more than the array holds); every call with
  *     n = nq <= 838,000 fits.  A call that would not fit returns CERT_EINVAL
  *     with the required size in cert_last_error(NULL); nothing is enqueued.
  *   - The first call on each device looks up the array's device address

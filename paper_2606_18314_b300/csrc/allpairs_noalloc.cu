@@ -82,8 +82,9 @@ extern "C" cert_status cert_allpairs_noalloc(const float *d_pos, int64_t n, int3
     if (nq < 0 || nq >= (int64_t(1) << 30)) return noalloc_fail(CERT_EINVAL, "bad query count");
     if (nq == 0) return CERT_OK;
 
-    // Same decomposition as cert_allpairs (512 queries per CTA, j-chunks filling
-    // whole waves), with the chunk count also capped by the scratch it needs.
+    // Same decomposition as cert_allpairs (512 queries per CTA, the j-chunk
+    // count from the same wave-time model), with the chunk count also capped by
+    // the scratch it needs.
     const int64_t nqb = (nq + kApQBlock - 1) / kApQBlock;
     const int64_t room = (int64_t)kNoAllocScratchBytes - (int64_t)align256(size_t(n) * sizeof(float4)) - 4096;
     const int64_t fit = room > 0 ? room / (nq * int64_t(6 * sizeof(float))) : 1;
