@@ -47,7 +47,9 @@ typedef enum {
     CERT_ECUDA = 3,    /* a CUDA runtime call failed; see cert_last_error          */
     CERT_ETIMEOUT = 4, /* (latched) a bounded device-side wait gave up             */
     CERT_EBOUND = 5,   /* (latched, warning) measured eps_t > declared eps         */
-    CERT_ESTATE = 6    /* call not valid in the context's current state            */
+    CERT_ESTATE = 6,   /* call not valid in the context's current state            */
+    CERT_EINTERNAL = 7 /* (latched, debug builds only: libcert_debug.so) an internal
+                          index check failed -- a bug in this library, never the caller's */
 } cert_status;
 
 typedef enum {

@@ -1,6 +1,10 @@
 """Build libcert.so in-tree for sm_103a with nvcc (no JIT, no torch extension).
 
-    python -m paper_2606_18314_b300.build [--force] [--verbose]
+    python -m paper_2606_18314_b300.build [--force] [--verbose] [--debug]
+
+--debug builds libcert_debug.so: the same sources with -DCERT_DEBUG_BOUNDS,
+whose kernels check the indices the release build relies on by construction
+and latch CERT_EINTERNAL on a violation (load it with CERT_LIB_VARIANT=debug).
 """
 from __future__ import annotations
 
@@ -12,6 +16,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcert.so")
+LIB_DEBUG = os.path.join(HERE, "libcert_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
            "-shared", "-cudart=static", "--expt-relaxed-constexpr"]
@@ -26,26 +31,26 @@ def deps():
         glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h"))
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = LIB_DEBUG if debug else LIB
+    if not force and not stale(lib):
+        return lib
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *ARCH, *NVFLAGS, "-I", os.path.join(os.path.dirname(HERE), "include"),
-           "-o", LIB, *sources()]
+    cmd = [nvcc, *ARCH, *NVFLAGS, *(["-DCERT_DEBUG_BOUNDS"] if debug else []),
+           "-I", os.path.join(os.path.dirname(HERE), "include"), "-o", lib, *sources()]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
         print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="--verbose" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv, debug="--debug" in sys.argv))

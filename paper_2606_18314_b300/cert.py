@@ -15,11 +15,12 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libcert.so")
+# CERT_LIB_VARIANT=debug loads the build with device index checks (libcert_debug.so)
+LIB_PATH = os.path.join(HERE, "libcert_debug.so" if os.environ.get("CERT_LIB_VARIANT") == "debug" else "libcert.so")
 
-CERT_OK, CERT_EINVAL, CERT_ENOMEM, CERT_ECUDA, CERT_ETIMEOUT, CERT_EBOUND, CERT_ESTATE = range(7)
+CERT_OK, CERT_EINVAL, CERT_ENOMEM, CERT_ECUDA, CERT_ETIMEOUT, CERT_EBOUND, CERT_ESTATE, CERT_EINTERNAL = range(8)
 STATUS_NAMES = ["CERT_OK", "CERT_EINVAL", "CERT_ENOMEM", "CERT_ECUDA", "CERT_ETIMEOUT", "CERT_EBOUND",
-                "CERT_ESTATE"]
+                "CERT_ESTATE", "CERT_EINTERNAL"]
 CERT_AUTO, CERT_INCREMENTAL, CERT_REBUILD, CERT_ALLPAIRS, CERT_THRESHOLD = range(5)
 STRATEGY = {"auto": CERT_AUTO, "incremental": CERT_INCREMENTAL, "rebuild": CERT_REBUILD,
             "allpairs": CERT_ALLPAIRS, "threshold": CERT_THRESHOLD}

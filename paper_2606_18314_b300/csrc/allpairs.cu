@@ -285,6 +285,7 @@ __global__ void k_allpairs_merge_step(const APArgs a, const APMergeOut o)
         merge_partials(a, sp, sp.n, i - sp.pt_off, t);
         const int n1 = (t.j0 != 0x7fffffff) ? t.j0 - sp.pt_off : -1;
         const int n2 = (t.j1 != 0x7fffffff) ? t.j1 - sp.pt_off : -1;
+        CERT_CHECK(sa.status, (unsigned)n1 < (unsigned)sp.n && (unsigned)n2 < (unsigned)sp.n);
         changed = n1 != sa.nn[i];
         sa.failed[i] = (uint8_t)changed;
         if (changed) {

@@ -674,6 +674,7 @@ cert_status cert_sync_result(cert_ctx *c, cert_scene_result *h_scenes)
     uint32_t st = 0;
     CK(c, cudaMemcpy(&st, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     CK(c, cudaMemset(c->status, 0, sizeof(uint32_t)));
+    if (st & ST_INDEX) return fail(c, CERT_EINTERNAL, "an internal index check failed (debug build)");
     if (st & ST_TIMEOUT) return fail(c, CERT_ETIMEOUT, "a bounded device wait gave up");
     if (st & ST_NONFINITE) return fail(c, CERT_EINVAL, "non-finite coordinate in the positions");
     if (st & ST_EBOUND) return fail(c, CERT_EBOUND, "measured eps_t exceeded the declared eps");

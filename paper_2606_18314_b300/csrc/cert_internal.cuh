@@ -22,7 +22,23 @@ constexpr uint32_t kSpinLimit = 1u << 22;              // bounded device waits
 constexpr int kNlognTable = 1 << 16;                   // k ln k table entries (FP64)
 
 // Latched device status bits (returned by cert_sync_result).
-enum : uint32_t { ST_TIMEOUT = 1u, ST_NONFINITE = 2u, ST_EBOUND = 4u };
+enum : uint32_t { ST_TIMEOUT = 1u, ST_NONFINITE = 2u, ST_EBOUND = 4u, ST_INDEX = 8u };
+
+// Debug builds (-DCERT_DEBUG_BOUNDS, libcert_debug.so): index checks at the
+// points where the release code relies on construction (search ranges inside
+// their scene, neighbour indices written into certificates); a failed check
+// latches ST_INDEX, which the host returns as CERT_EINTERNAL.  In release
+// builds the checks compile to nothing.
+#ifdef CERT_DEBUG_BOUNDS
+#define CERT_CHECK(status, cond)                        \
+    do {                                                \
+        if (!(cond)) atomicOr((status), certk::ST_INDEX); \
+    } while (0)
+#else
+#define CERT_CHECK(status, cond) \
+    do {                         \
+    } while (0)
+#endif
 
 // Step kernel modes.
 enum : int { MODE_INIT = 0, MODE_STEP = 1, MODE_REBUILD = 2 };

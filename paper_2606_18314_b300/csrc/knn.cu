@@ -393,6 +393,7 @@ template <int DIM, int KH>
 __device__ __forceinline__ void visit_slots(const KnnArgs &a, int lo, int hi, int step, const float4 p, int self,
                                             float (&hd)[KH], int (&hj)[KH])
 {
+    CERT_CHECK(a.status, lo >= 0 && hi <= 2 * a.n);
     for (int s = lo; s < hi; s += step) {
         const float4 q = a.spos[s];
         const int j = __float_as_int(q.w);
@@ -558,6 +559,9 @@ __device__ __forceinline__ int write_list(const KnnArgs &a, int i, const float (
         changed = set_changed<KB, KH>(oj, hj, k);
         a.failed[i] = (uint8_t)changed;
     }
+#pragma unroll
+    for (int r = 0; r < KH; ++r)
+        if (r <= k) CERT_CHECK(a.status, (unsigned)hj[r] < (unsigned)n);   // ranks 0 .. k always hold a point
 #pragma unroll
     for (int r = 0; r < KH; ++r)
         if (r < S) {
@@ -1156,6 +1160,7 @@ cert_status cert_knn_sync_result(cert_knn_ctx *c, cert_knn_result *out)
     uint32_t st = 0;
     KCK(cudaMemcpy(&st, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     KCK(cudaMemset(c->status, 0, sizeof(uint32_t)));
+    if (st & ST_INDEX) return knn_fail(CERT_EINTERNAL, "an internal index check failed (debug build)");
     if (st & ST_NONFINITE) return knn_fail(CERT_EINVAL, "non-finite coordinate in the positions");
     if (st & ST_EBOUND) return knn_fail(CERT_EBOUND, "measured eps_t exceeded the declared eps");
     return CERT_OK;

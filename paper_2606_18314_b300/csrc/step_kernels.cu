@@ -643,6 +643,9 @@ struct SearchCtx {
     int g;
     float inv_g;
     bool dense;
+#ifdef CERT_DEBUG_BOUNDS
+    uint32_t *status;
+#endif
 };
 
 // Visit the sorted slots [lo, hi) of the scene.  The range is widened to whole
@@ -659,6 +662,7 @@ __device__ __forceinline__ void visit_range(const SearchCtx &c, int lo, int hi, 
     if (lo >= hi) return;
     const int q0 = (lo + c.pad) >> 2;
     const int q1 = (hi + c.pad + 3) >> 2;
+    CERT_CHECK(c.status, q0 >= ((c.pt_off + c.pad) >> 2) && q1 <= ((c.pt_off + c.n + c.pad + 3) >> 2));
     const float4 *r = c.squad + (size_t)q0 * 4;
     float4 X = r[0], Y = r[1];
     float4 Z = (DIM == 3) ? r[2] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -702,6 +706,13 @@ __device__ __forceinline__ void visit_quad_rows(const SearchCtx &c, const int2 *
         qe = rr.y;
     }
     if (q >= qe) return;
+#ifdef CERT_DEBUG_BOUNDS
+    const int qmin = (c.pt_off + c.pad) >> 2, qmax = (c.pt_off + c.n + c.pad + 3) >> 2;
+    for (int kk = 0; kk < NR; ++kk) {
+        const int2 rk = rng[kk * kThreads];
+        CERT_CHECK(c.status, rk.x >= rk.y || (rk.x >= qmin && rk.y <= qmax));
+    }
+#endif
     const float4 *r = c.squad + (size_t)q * 4;
     float4 X = r[0], Y = r[1];
     float4 Z = (DIM == 3) ? r[2] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -934,6 +945,8 @@ __device__ __forceinline__ SearchOut write_certificate(const StepArgs &a, const 
     SearchOut o = {0, 0, 0, 0, 0.0};
     const int n1 = (t.j0 != 0x7fffffff) ? t.j0 - sp.pt_off : -1;
     const int n2 = (t.j1 != 0x7fffffff) ? t.j1 - sp.pt_off : -1;
+    CERT_CHECK(a.status, (unsigned)(gi - sp.pt_off) < (unsigned)sp.n && (unsigned)n1 < (unsigned)sp.n &&
+                             (unsigned)n2 < (unsigned)sp.n);
     if (a.mode == MODE_STEP) {
         o.changed = n1 != a.nn[gi];
         a.failed[gi] = (uint8_t)o.changed;
@@ -997,6 +1010,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
             SearchCtx c;
             c.squad = a.squad;
             c.bstart = a.bucket_start;
+#ifdef CERT_DEBUG_BOUNDS
+            c.status = a.status;
+#endif
             c.p = q;
             c.px2 = pack2(q.x, q.x);
             c.py2 = pack2(q.y, q.y);

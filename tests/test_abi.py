@@ -133,3 +133,17 @@ def test_knn_rejects_bad_arguments_without_a_gpu(L):
     assert ctypes.sizeof(cert.cert_knn_config) == 24
     assert ctypes.sizeof(cert.cert_knn_result) == 40
     assert ctypes.sizeof(cert.cert_knn_views) == 5 * 8 + 8 + 4 + 4
+
+
+def test_debug_variant_loads_and_exports_every_symbol():
+    """libcert_debug.so (index-checked kernels) is selected by CERT_LIB_VARIANT=debug
+    and exports the same boundary."""
+    import subprocess
+    import sys
+    cbuild.build(debug=True)
+    code = ("from paper_2606_18314_b300 import cert; L = cert.lib(); "
+            "assert cert.LIB_PATH.endswith('libcert_debug.so'); "
+            "missing = [n for n in cert.EXPORTS if not hasattr(L, n)]; assert not missing, missing; print('ok')")
+    env = dict(os.environ, CERT_LIB_VARIANT="debug")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and "ok" in out.stdout, out.stderr[-2000:]
