@@ -1258,7 +1258,9 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
     case PH_FINALIZE:
         if (a.mode == MODE_STEP && (a.audit & CERT_AUDIT_GEOMETRY))
             k_geometry<DIM><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(a);
-        if (cudaPeekAtLastError() == cudaSuccess) k_finalize<<<nblk(a.n_scenes, 128), 128, 0, st>>>(a);
+        // one thread per scene, 32 per block: the FP64 logarithms of the entropies spread over
+        // n_scenes / 32 SMs instead of a few
+        if (cudaPeekAtLastError() == cudaSuccess) k_finalize<<<nblk(a.n_scenes, 32), 32, 0, st>>>(a);
         break;
     default: return cudaErrorInvalidValue;
     }
