@@ -399,6 +399,20 @@ __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p)
     return v;
 }
 
+// A 64-bit word that carries everything its reader needs (a flag and a value)
+// needs no ordering against other memory: relaxed, single-copy atomic access.
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // ----------------------------------------------------------------------------- warp helpers
 
 constexpr unsigned kFull = 0xffffffffu;

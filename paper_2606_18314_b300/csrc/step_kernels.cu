@@ -125,23 +125,26 @@ __global__ void __launch_bounds__(kThreads) k_prepare(const StepArgs a)
 // ============================================================================ k_scan
 
 // Publish this tile's aggregate and look back over predecessors for the
-// exclusive prefix (single-pass chained scan).  Called by warp 0 only.  Every
-// wait is bounded; on expiry the status word records a timeout and the
+// exclusive prefix (single-pass chained scan).  Called by warp 0 only.  A
+// status word is (flag << 32) | value with flag 1 = the tile's aggregate,
+// 2 = its inclusive prefix, 0 = not yet published; the word is all a reader
+// needs, so relaxed accesses suffice (acquire / release cost 6 us a step).
+// Every wait is bounded; on expiry the status word records a timeout and the
 // (incorrect) partial prefix is used so that the kernel still terminates.
 __device__ uint32_t lookback(uint64_t *tstat, int tile, uint32_t aggregate, uint32_t *status)
 {
     const int lane = threadIdx.x & 31;
     if (tile == 0) {
-        if (lane == 0) st_release_u64(&tstat[0], (2ull << 32) | aggregate);
+        if (lane == 0) st_relaxed_u64(&tstat[0], (2ull << 32) | aggregate);
         return 0u;
     }
-    if (lane == 0) st_release_u64(&tstat[tile], (1ull << 32) | aggregate);
+    if (lane == 0) st_relaxed_u64(&tstat[tile], (1ull << 32) | aggregate);
     uint32_t excl = 0u;
     int p = tile - 1;
     uint32_t spins = 0u;
     for (;;) {
         const int idx = p - lane;
-        const uint64_t v = (idx >= 0) ? ld_acquire_u64(&tstat[idx]) : (2ull << 32);
+        const uint64_t v = (idx >= 0) ? ld_relaxed_u64(&tstat[idx]) : (2ull << 32);   // before tile 0: prefix 0
         const uint32_t flag = (uint32_t)(v >> 32);
         const unsigned incl = __ballot_sync(kFull, flag == 2u);
         const unsigned notready = __ballot_sync(kFull, flag == 0u);
@@ -161,7 +164,7 @@ __device__ uint32_t lookback(uint64_t *tstat, int tile, uint32_t aggregate, uint
         if (fi < 32) break;
         p -= 32;
     }
-    if (lane == 0) st_release_u64(&tstat[tile], (2ull << 32) | (excl + aggregate));
+    if (lane == 0) st_relaxed_u64(&tstat[tile], (2ull << 32) | (excl + aggregate));
     return excl;
 }
 
