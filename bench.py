@@ -312,6 +312,57 @@ def knn_phase_bytes(ph, n, dim, k, buckets, n_searched, n_refreshed):
     return 0
 
 
+def launch_floor(torch, steps, nodes_per_step, stream):
+    """ms per step of a CUDA graph holding ``nodes_per_step`` dependent
+    one-element kernels per step: the replay cost of a step's launches alone."""
+    x = torch.zeros(1, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(steps * nodes_per_step):
+            x.add_(1.0)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def single_scene_report(cert, torch, steps, stream):
+    """The single-scene configurations (N = 1,000 d = 2; 16,000 d = 3;
+    262,144 d = 3 clustered), whose state fits in L2: step time under graph
+    replay for each plain strategy, against the launch floor of the same
+    number of graph nodes (7 kernels and 1 memset per step)."""
+    F = 8
+    C = 2 * F
+    K = max(C, (steps // C) * C)
+    floor = launch_floor(torch, K, KERNELS_PER_STEP + 1, stream)
+    out = {"steps": K, "floor_ms_per_step": floor,
+           "floor": f"CUDA graph of {KERNELS_PER_STEP + 1} dependent one-element kernels per step", "rows": []}
+    for name in ("c1", "c2", "c3"):
+        frames, offsets, eps, cfg = make_workload(name, 0, F)
+        n, dim = frames.shape[1], frames.shape[2]
+        dev = torch.from_numpy(frames).cuda()
+        row = {"workload": cfg["workload"], "n": n, "dim": dim, "eps": eps}
+        for strat in ("incremental", "rebuild"):
+            ctx = cert.Context(dev[0])
+            for k in range(C):            # one eager cycle: back at frame 0
+                ctx.step(dev[cycle_index(k, F)], eps, cert.STRATEGY[strat])
+            ms, _ = graph_loop(ctx, dev, F, eps, cert.STRATEGY[strat], K, True, stream, torch)
+            res, rc = ctx.sync(raise_on_status=False)
+            assert rc == cert.CERT_OK and int(res["n_missed"].sum()) == 0, f"{name} {strat}: rc {rc}"
+            ctx.close()
+            row[f"{strat}_ms_per_step"] = ms / K
+            row[f"{strat}_point_updates_per_s"] = n * K / (ms * 1e-3)
+            row[f"{strat}_x_floor"] = (ms / K) / floor
+        out["rows"].append(row)
+        del dev
+    return out
+
+
 def knn_report(cert, torch, steps, peaks, stream):
     """k-nearest-neighbour certificates (the richer certificates the paper
     leaves open): point-updates/s with the steps replayed from a CUDA graph,
@@ -385,6 +436,8 @@ def main():
     ap.add_argument("--knn-steps", type=int, default=240,
                     help="graph-replayed steps per k-nearest-neighbour case (0: skip)")
     ap.add_argument("--compare-steps", type=int, default=256)
+    ap.add_argument("--single-steps", type=int, default=256,
+                    help="graph-replayed steps per single-scene configuration (0 to skip)")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--allpairs-sizes", default="40000,80000,200000",
@@ -565,6 +618,11 @@ def main():
     if args.knn_steps > 0 and rank == 0:
         knn = knn_report(cert, torch, args.knn_steps, load_peaks()[0], stream)
 
+    # ---- the single-scene configurations against the launch floor
+    single = None
+    if args.single_steps > 0 and rank == 0 and args.workload == "batched":
+        single = single_scene_report(cert, torch, args.single_steps, stream)
+
     # ---- per-phase timing (CUDA events on the launching stream), same workload, eager
     P = max(1, args.prof_steps)
     ctx.profile_begin(P)
@@ -683,7 +741,7 @@ def main():
                 "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
                 "step_counts": step_counts, "compare": compare, "regret": regret, "frontier_rules": rules,
-                "matched_pair": matched_pair, "knn": knn, "allpairs": allpairs,
+                "matched_pair": matched_pair, "knn": knn, "single_scene": single, "allpairs": allpairs,
                 "status": cert.STATUS_NAMES[rc] if 0 <= rc < len(cert.STATUS_NAMES) else rc}
         print(json.dumps(line), flush=True)
     ctx.close()
