@@ -13,6 +13,7 @@ namespace certk {
 
 constexpr int kThreads = 256;
 constexpr int kScanItems = 8;                          // items per thread in a scan tile
+constexpr int kScanLatencyTiles = 3 * 148;             // scan grids below this: latency issue order
 constexpr int kScanTile = kThreads * kScanItems;       // 2048 items per tile
 constexpr int kSearchChunk = 4 * kThreads;             // sorted slots per search CTA
 constexpr int kMedianSample = 1024;                    // points sampled for the medians

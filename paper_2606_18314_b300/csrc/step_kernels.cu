@@ -168,7 +168,12 @@ __device__ uint32_t lookback(uint64_t *tstat, int tile, uint32_t aggregate, uint
     return excl;
 }
 
-template <int DIM>
+// LAT selects the issue order for grids smaller than one wave (a small scene,
+// where a tile's per-thread chain of dependent accesses is the kernel's
+// time): the frontier items' entropy cells are loaded with the flags and their
+// atomics issued back to back.  The default order keeps 48 registers, five
+// resident CTAs per SM, for the many-tile grids that are bound by resident CTAs.
+template <int DIM, bool LAT>
 __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
 {
     __shared__ uint32_t s_warp[kThreads / 32];
@@ -220,12 +225,14 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     uint32_t rho = 0u;                 // bit k: item k flagged by the rho heuristic
     static_assert(kScanItems <= 32, "rho flags fit one word");
     int sc[kScanItems];
+    int hc[kScanItems];                // LAT: entropy cell of a frontier item, loaded early
     uint32_t sum = 0u;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const int i = base + k;
         f[k] = 0u;
         sc[k] = -1;
+        hc[k] = 0;
         if (i < a.n_total) {
             const int s = a.scene_of[i];
             sc[k] = s;
@@ -273,6 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
                 rho |= r << k;
             }
             a.inF[i] = (uint8_t)(f[k] | (r << 1));
+            if (LAT && f[k]) hc[k] = a.hcell[i];
         }
         sum += f[k];
     }
@@ -288,11 +296,46 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     // locally and reduce once per warp; a scene change inside them is flushed directly
     int cur = -1, acc_first = 0, acc_rho = 0;
     double acc_dl = 0.0;
+    int old[kScanItems];               // LAT: the atomics' results, used after all are issued
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const int i = base + k;
         const int s = sc[k];
+        old[k] = -1;
         if (s >= 0) {
+            if (!LAT && s != cur) {
+                if (cur >= 0 && (acc_first || acc_dl != 0.0 || acc_rho)) {
+                    if (acc_first) atomicAdd(&a.acc[cur].frontier_cells, acc_first);
+                    if (acc_dl != 0.0) atomicAdd(&a.acc[cur].s_front, acc_dl);
+                    if (acc_rho) atomicAdd(&a.acc[cur].n_rho, acc_rho);
+                }
+                cur = s;
+                acc_first = 0;
+                acc_dl = 0.0;
+                acc_rho = 0;
+            }
+            if (!LAT) acc_rho += (int)((rho >> k) & 1u);
+            const SceneParams &sp = a.sp[s];
+            if (i == sp.pt_off) a.fstart[s] = (int)run;
+            if (f[k]) {
+                if (run < (uint32_t)a.n_total) a.frontier[run] = i - sp.pt_off;
+                if (LAT) {
+                    old[k] = atomicAdd(&a.hcand[sp.h_off + hc[k]], 1);
+                } else {
+                    const int o = atomicAdd(&a.hcand[sp.h_off + a.hcell[i]], 1);
+                    acc_first += o == 0;
+                    acc_dl += nlogn_step(a.nlogn, o);
+                }
+            }
+            if (i == a.n_total - 1) a.fstart[a.n_scenes] = (int)(run + f[k]);
+        }
+        run += f[k];
+    }
+    if (LAT) {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int s = sc[k];
+            if (s < 0) continue;
             if (s != cur) {
                 if (cur >= 0 && (acc_first || acc_dl != 0.0 || acc_rho)) {
                     if (acc_first) atomicAdd(&a.acc[cur].frontier_cells, acc_first);
@@ -305,17 +348,11 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
                 acc_rho = 0;
             }
             acc_rho += (int)((rho >> k) & 1u);
-            const SceneParams &sp = a.sp[s];
-            if (i == sp.pt_off) a.fstart[s] = (int)run;
-            if (f[k]) {
-                if (run < (uint32_t)a.n_total) a.frontier[run] = i - sp.pt_off;
-                const int old = atomicAdd(&a.hcand[sp.h_off + a.hcell[i]], 1);
-                acc_first += old == 0;
-                acc_dl += nlogn_step(a.nlogn, old);
+            if (old[k] >= 0) {
+                acc_first += old[k] == 0;
+                acc_dl += nlogn_step(a.nlogn, old[k]);
             }
-            if (i == a.n_total - 1) a.fstart[a.n_scenes] = (int)(run + f[k]);
         }
-        run += f[k];
     }
     const unsigned m = scene_run_mask(cur);
     const int fc = run_sum_i32(m, acc_first);
@@ -1251,7 +1288,12 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
 {
     switch (phase) {
     case PH_PREPARE: k_prepare<DIM><<<nblk(a.n_total, kThreads * kPrepPer), kThreads, 0, st>>>(a); break;
-    case PH_SCAN: k_scan<DIM><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a); break;
+    case PH_SCAN:
+        if (a.ntiles_b + a.ntiles_p < kScanLatencyTiles)
+            k_scan<DIM, true><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a);
+        else
+            k_scan<DIM, false><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a);
+        break;
     case PH_SELECT: k_select<DIM><<<a.n_scenes, kThreads, 0, st>>>(a); break;
     case PH_SCATTER: k_scatter_refresh<DIM><<<nblk(a.n_total, kThreads * kScatPer), kThreads, 0, st>>>(a); break;
     case PH_SEARCH:
