@@ -74,7 +74,7 @@ def phase_bytes(ph, N, dim, n_buckets, n_front, n_searched, zero_bytes, n_tried=
 # DRAM bytes (read + write) per k_search launch from the ncu capture of the batched
 # 512-scene incremental step (profiles/k_search_batched_512_incremental.md); valid for
 # that workload and kernel version only.
-SEARCH_TRAFFIC_BATCHED = 173.18e6
+SEARCH_TRAFFIC_BATCHED = 172.77e6
 
 
 def load_peaks():

@@ -16,6 +16,8 @@ constexpr int kScanItems = 8;                          // items per thread in a 
 constexpr int kScanLatencyTiles = 3 * 148;             // scan grids below this: latency issue order
 constexpr int kScanTile = kThreads * kScanItems;       // 2048 items per tile
 constexpr int kSearchChunk = 4 * kThreads;             // sorted slots per search CTA
+constexpr int kSearchSmallGrid = 4 * 148;              // half-size search chunks up to one wave
+static_assert(kScanTile % kSearchChunk == 0, "the flag padding (a multiple of the scan tile) covers every search chunk");
 constexpr int kMedianSample = 1024;                    // points sampled for the medians
 constexpr int kMaxSearchRes = 2048;                    // search-grid cells per axis, cap
 constexpr int kMaxExtend = 16;                         // face extensions before a warp scans the scene

@@ -1008,21 +1008,29 @@ __device__ __forceinline__ SearchOut write_certificate(const StepArgs &a, const 
     return o;
 }
 
-// One CTA compacts the flagged slots of kSearchChunk consecutive sorted slots
+// One CTA compacts the flagged slots of CHUNK consecutive sorted slots
 // (ascending, so a warp's queries are neighbours and share most rows), then
-// searches them kThreads at a time.
-template <int DIM>
+// searches them kThreads at a time.  CHUNK is kSearchChunk; a grid that fits
+// one wave even at half that (a small or single scene) takes half-size chunks,
+// so that a CTA's queries fit one round of kThreads instead of spilling a few
+// stragglers into a second round on the critical path.
+template <int DIM, int CHUNK>
 __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 64 registers: 4 CTAs per SM
 {
     constexpr int NR = (DIM == 3) ? 9 : 3;
-    constexpr int PER = kSearchChunk / kThreads;   // slots per thread in the compaction
-    static_assert(PER == 4, "the flag load below reads four flags at once");
+    constexpr int PER = CHUNK / kThreads;   // slots per thread in the compaction
+    static_assert(PER == 1 || PER == 2 || PER == 4, "the flag load below reads one, two or four flags at once");
     __shared__ uint32_t s_warp[kThreads / 32];
-    __shared__ int s_list[kSearchChunk];
+    __shared__ int s_list[CHUNK];
     __shared__ int2 s_rng[(kMaxRows > NR ? kMaxRows : NR) * kThreads];   // per-thread row ranges, column-major
-    const int base = blockIdx.x * kSearchChunk + threadIdx.x * PER;
-    // flags beyond n_total are zero up to the padded length (a multiple of the chunk)
-    const uint32_t fw = (base < a.n_total) ? *reinterpret_cast<const uint32_t *>(a.sflag + base) : 0u;
+    const int base = blockIdx.x * CHUNK + threadIdx.x * PER;
+    // flags beyond n_total are zero up to the padded length (a multiple of the
+    // scan tile, itself a multiple of CHUNK); each flag byte is 0 or 1
+    uint32_t fw = 0u;
+    if (base < a.n_total)
+        fw = (PER == 4)   ? *reinterpret_cast<const uint32_t *>(a.sflag + base)
+             : (PER == 2) ? (uint32_t)*reinterpret_cast<const uint16_t *>(a.sflag + base)
+                          : (uint32_t)a.sflag[base];
     uint32_t count;
     uint32_t pre = block_exclusive_scan(__popc(fw), &count, s_warp);
 #pragma unroll
@@ -1297,7 +1305,12 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
     case PH_SELECT: k_select<DIM><<<a.n_scenes, kThreads, 0, st>>>(a); break;
     case PH_SCATTER: k_scatter_refresh<DIM><<<nblk(a.n_total, kThreads * kScatPer), kThreads, 0, st>>>(a); break;
     case PH_SEARCH:
-        k_search<DIM><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
+        if (nblk(a.n_total, kSearchChunk / 4) <= kSearchSmallGrid)
+            k_search<DIM, kSearchChunk / 4><<<nblk(a.n_total, kSearchChunk / 4), kThreads, 0, st>>>(a);
+        else if (nblk(a.n_total, kSearchChunk / 2) <= kSearchSmallGrid)
+            k_search<DIM, kSearchChunk / 2><<<nblk(a.n_total, kSearchChunk / 2), kThreads, 0, st>>>(a);
+        else
+            k_search<DIM, kSearchChunk><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
         if (cudaPeekAtLastError() == cudaSuccess) k_far<DIM><<<kFarCtas, kThreads, 0, st>>>(a);
         break;
     case PH_FINALIZE:
