@@ -44,7 +44,7 @@ namespace certk {
 constexpr int kPrepPer = 4;
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_prepare(const StepArgs a)
+__global__ void __launch_bounds__(kThreads, 5) k_prepare(const StepArgs a)   // 48 registers: 5 CTAs per SM
 {
     const int base = blockIdx.x * (kThreads * kPrepPer) + threadIdx.x;
     int s[kPrepPer];
