@@ -38,19 +38,21 @@ namespace certk {
 
 // ============================================================================ k_prepare
 
-// kPrepPer points per thread (strided by kThreads, so a warp's lanes still hold
+// PER points per thread (strided by kThreads, so a warp's lanes still hold
 // consecutive points): the loads, atomics and stores of the points are issued
-// together, overlapping their latencies.
+// together, overlapping their latencies.  kPrepPer for grids that fill the GPU;
+// a small grid takes fewer per thread and more CTAs (chosen at the launch).
 constexpr int kPrepPer = 4;
+constexpr int kSmallGridPrepare = 5 * 148;   // one wave of k_prepare (48 registers)
 
-template <int DIM>
+template <int DIM, int PER>
 __global__ void __launch_bounds__(kThreads, 5) k_prepare(const StepArgs a)   // 48 registers: 5 CTAs per SM
 {
-    const int base = blockIdx.x * (kThreads * kPrepPer) + threadIdx.x;
-    int s[kPrepPer];
-    float4 p[kPrepPer], po[kPrepPer];
+    const int base = blockIdx.x * (kThreads * PER) + threadIdx.x;
+    int s[PER];
+    float4 p[PER], po[PER];
 #pragma unroll
-    for (int k = 0; k < kPrepPer; ++k) {
+    for (int k = 0; k < PER; ++k) {
         const int i = base + k * kThreads;
         s[k] = -1;
         p[k] = po[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -67,10 +69,10 @@ __global__ void __launch_bounds__(kThreads, 5) k_prepare(const StepArgs a)   // 
             }
         }
     }
-    unsigned dbits[kPrepPer];
-    int first[kPrepPer], rank[kPrepPer], b[kPrepPer], hc[kPrepPer];
+    unsigned dbits[PER];
+    int first[PER], rank[PER], b[PER], hc[PER];
 #pragma unroll
-    for (int k = 0; k < kPrepPer; ++k) {
+    for (int k = 0; k < PER; ++k) {
         const int i = base + k * kThreads;
         dbits[k] = 0u;
         first[k] = 0;
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_prepare(const StepArgs a)   // 
         }
     }
 #pragma unroll
-    for (int k = 0; k < kPrepPer; ++k) {
+    for (int k = 0; k < PER; ++k) {
         const int i = base + k * kThreads;
         if (s[k] >= 0) {
             a.brank[i] = make_int2(b[k], rank[k]);
@@ -545,20 +547,22 @@ __global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
 
 // ============================================================================ k_scatter_refresh
 
-// kScatPer points per thread (strided by kThreads), their loads issued together.
+// PER points per thread (strided by kThreads), their loads issued together:
+// kScatPer for grids that fill the GPU, one for a small grid.
 constexpr int kScatPer = 2;
+constexpr int kSmallGridScatter = 6 * 148;   // one wave of k_scatter_refresh (42 registers)
 
-template <int DIM>
+template <int DIM, int PER>
 __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
 {
-    const int base = blockIdx.x * (kThreads * kScatPer) + threadIdx.x;
+    const int base = blockIdx.x * (kThreads * PER) + threadIdx.x;
     const bool step = a.mode == MODE_STEP;
-    int s[kScatPer], na[kScatPer], nb[kScatPer], nc[kScatPer];
-    int2 br[kScatPer];
-    float4 p[kScatPer];
-    float Lold[kScatPer];
+    int s[PER], na[PER], nb[PER], nc[PER];
+    int2 br[PER];
+    float4 p[PER];
+    float Lold[PER];
 #pragma unroll
-    for (int k = 0; k < kScatPer; ++k) {
+    for (int k = 0; k < PER; ++k) {
         const int i = base + k * kThreads;
         s[k] = -1;
         na[k] = nb[k] = nc[k] = -1;
@@ -575,10 +579,10 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
             }
         }
     }
-    int changed[kScatPer], missed[kScatPer], first[kScatPer], hit[kScatPer];
-    double dl[kScatPer];
+    int changed[PER], missed[PER], first[PER], hit[PER];
+    double dl[PER];
 #pragma unroll
-    for (int k = 0; k < kScatPer; ++k) {
+    for (int k = 0; k < PER; ++k) {
         const int i = base + k * kThreads;
         changed[k] = missed[k] = first[k] = hit[k] = 0;
         dl[k] = 0.0;
@@ -651,7 +655,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
     }
     if (!step) return;  // uniform across the grid
 #pragma unroll
-    for (int k = 0; k < kScatPer; ++k) {
+    for (int k = 0; k < PER; ++k) {
         const unsigned m = scene_run_mask(s[k]);
         const int ncg = run_sum_i32(m, changed[k]);
         if (__any_sync(kFull, ncg != 0)) {
@@ -1295,7 +1299,15 @@ template <int DIM>
 static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
 {
     switch (phase) {
-    case PH_PREPARE: k_prepare<DIM><<<nblk(a.n_total, kThreads * kPrepPer), kThreads, 0, st>>>(a); break;
+    case PH_PREPARE:
+        // the fewest points per thread whose grid still fits one wave (5 CTAs per SM)
+        if (nblk(a.n_total, kThreads) <= kSmallGridPrepare)
+            k_prepare<DIM, 1><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(a);
+        else if (nblk(a.n_total, kThreads * 2) <= kSmallGridPrepare)
+            k_prepare<DIM, 2><<<nblk(a.n_total, kThreads * 2), kThreads, 0, st>>>(a);
+        else
+            k_prepare<DIM, kPrepPer><<<nblk(a.n_total, kThreads * kPrepPer), kThreads, 0, st>>>(a);
+        break;
     case PH_SCAN:
         if (a.ntiles_b + a.ntiles_p < kScanLatencyTiles)
             k_scan<DIM, true><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a);
@@ -1303,7 +1315,12 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
             k_scan<DIM, false><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a);
         break;
     case PH_SELECT: k_select<DIM><<<a.n_scenes, kThreads, 0, st>>>(a); break;
-    case PH_SCATTER: k_scatter_refresh<DIM><<<nblk(a.n_total, kThreads * kScatPer), kThreads, 0, st>>>(a); break;
+    case PH_SCATTER:
+        if (nblk(a.n_total, kThreads) <= kSmallGridScatter)
+            k_scatter_refresh<DIM, 1><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(a);
+        else
+            k_scatter_refresh<DIM, kScatPer><<<nblk(a.n_total, kThreads * kScatPer), kThreads, 0, st>>>(a);
+        break;
     case PH_SEARCH:
         if (nblk(a.n_total, kSearchChunk / 4) <= kSearchSmallGrid)
             k_search<DIM, kSearchChunk / 4><<<nblk(a.n_total, kSearchChunk / 4), kThreads, 0, st>>>(a);

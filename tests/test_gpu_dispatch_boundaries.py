@@ -8,6 +8,10 @@ its launch shape.  The certificates must be the same on either side.
   tiles of 2048) has fewer than 3 x 148 tiles.  At d = 3 with N in
   (262,144, 524,288] there are 257 bucket tiles, so the switch is at
   N = 380,928 | 380,929.
+* k_prepare takes 1, 2 or 4 points per thread, the fewest whose grid of
+  256-thread CTAs fits 5 x 148: N = 189,440 | 189,441 and 378,880 | 378,881.
+* k_scatter_refresh takes 1 point per thread while ceil(N / 256) <= 6 x 148,
+  else 2: N = 227,328 | 227,329.
 
 Each scene is stepped twice incrementally and once by rebuild. After each step
 every certificate must equal the GPU all-pairs pass bit for bit; that pass is
@@ -31,7 +35,8 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("n", [151552, 151553, 303104, 303105, 380928, 380929])
+@pytest.mark.parametrize("n", [151552, 151553, 189440, 189441, 227328, 227329, 303104, 303105, 378880, 378881,
+                               380928, 380929])
 def test_both_sides_of_each_launch_shape_switch(torch, n):
     from paper_2606_18314_b300 import cert
     m = scenes.Motion("uniform_brownian", n, 3, 1e-3, seed=n, steps=8)
