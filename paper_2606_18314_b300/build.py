@@ -8,10 +8,12 @@ and latch CERT_EINTERNAL on a violation (load it with CERT_LIB_VARIANT=debug).
 """
 from __future__ import annotations
 
+import concurrent.futures
 import glob
 import os
 import subprocess
 import sys
+import tempfile
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -38,17 +40,37 @@ def stale(lib: str = LIB) -> bool:
     return any(os.path.getmtime(p) > t for p in deps())
 
 
+def _compile(nvcc, src, obj, extra, verbose):
+    cmd = [nvcc, *ARCH, *[f for f in NVFLAGS if f not in ("-shared", "-cudart=static")], *extra,
+           "-I", os.path.join(os.path.dirname(HERE), "include"), "-c", "-o", obj, src]
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+    return subprocess.run(cmd, capture_output=True, text=True), cmd
+
+
 def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile every source to an object in parallel (one nvcc each; no
+    relocatable device code crosses files), then link the shared library."""
     lib = LIB_DEBUG if debug else LIB
     if not force and not stale(lib):
         return lib
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *ARCH, *NVFLAGS, *(["-DCERT_DEBUG_BOUNDS"] if debug else []),
-           "-I", os.path.join(os.path.dirname(HERE), "include"), "-o", lib, *sources()]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), flush=True)
-    subprocess.run(cmd, check=True)
+    extra = ["-DCERT_DEBUG_BOUNDS"] if debug else []
+    srcs = sources()
+    with tempfile.TemporaryDirectory(prefix="certbuild_") as tmp:
+        objs = [os.path.join(tmp, os.path.basename(f) + ".o") for f in srcs]
+        with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+            results = list(ex.map(lambda so: _compile(nvcc, so[0], so[1], extra, verbose), zip(srcs, objs)))
+        for r, cmd in results:
+            if verbose:
+                print(" ".join(cmd), flush=True)
+                sys.stdout.write(r.stdout + r.stderr)
+            if r.returncode != 0:
+                sys.stderr.write(r.stdout + r.stderr)
+                raise subprocess.CalledProcessError(r.returncode, cmd)
+        link = [nvcc, *ARCH, "-shared", "-cudart=static", "-Xcompiler", "-fPIC", "-o", lib + ".tmp", *objs]
+        subprocess.run(link, check=True)
+        os.replace(lib + ".tmp", lib)
     return lib
 
 
