@@ -10,9 +10,13 @@ or rebuild, failure marks, H(F_t), audit -- over all scenes of the workload.
 
 Default workload: 512 independent scenes, N log-uniform in [500, 16000],
 d = 3, the five motion families mixed (scene s takes family s mod 5),
-eps = 1e-3.  The motion is a ping-pong over F+1 pre-generated frames
-(forward to frame F, back to frame 0), every step within eps; the cycle
-(2F steps) is captured once as a CUDA graph and replayed.
+eps = 1e-3.  The motion is F = 100 pre-generated forward frames (the
+benchmark configuration's 100 steps); the warm-up steps walk forward from
+frame 0 and the timed steps continue forward from there.  Past frame F the
+walk turns back (a ping-pong over the F+1 frames), every step within eps.
+The schedule repeats every 2F steps, so at most two CUDA graphs (a 2F-step
+one replayed, and a remainder) are captured and replayed.  `forward_100`
+reports the 100 forward steps alone, from frame 0, as one graph.
 
 Inputs are synthetic (seeded Philox motion families; no dataset).  The
 working set (positions, certificates, index) exceeds the 126 MB L2, so no
@@ -71,10 +75,13 @@ def phase_bytes(ph, N, dim, n_buckets, n_front, n_searched, zero_bytes, n_tried=
     return 0
 
 
-# DRAM bytes (read + write) per k_search launch from the ncu capture of the batched
-# 512-scene incremental step (profiles/k_search_batched_512_incremental.md); valid for
-# that workload and kernel version only.
-SEARCH_TRAFFIC_BATCHED = 172.77e6
+# DRAM bytes (read + write) of one k_search launch on the batched 512-scene
+# incremental step, from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), with the source fingerprint of the step kernels'
+# translation unit the capture ran on.  The bench line carries the figure only
+# while the loaded library reports the same fingerprint; after any change to
+# the kernels it reports null until the capture is taken again.
+SEARCH_TRAFFIC = {"bytes": None, "fingerprint": None, "commit": None}
 
 
 def load_peaks():
@@ -136,13 +143,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_workload(name, rank, frames, n_scenes=512, family=None):
+def make_workload(name, rank, frames, n_scenes=512, family=None, workers=1):
+    """(frames [F+1][N][dim], scene offsets, eps, config) of a named workload;
+    ``workers`` > 1 generates the batched scenes in a pool of spawned processes."""
     if name == "batched":
         bm = scenes.BatchMotion.mixed(n_scenes=n_scenes, dim=3, eps=1e-3, seed=4 + 1000 * rank, steps=100)
         if family:   # diagnostics: every scene of one family (same sizes and seeds)
             bm = scenes.BatchMotion([scenes.Motion(family, m.n, 3, 1e-3, seed=m.seed, steps=100)
                                      for m in bm.scenes])
-        return bm.frames(frames), bm.offsets, 1e-3, {
+        fr = bm.frames_parallel(frames, workers) if workers > 1 and frames >= 8 else bm.frames(frames)
+        return fr, bm.offsets, 1e-3, {
             "workload": f"batched-{n_scenes}-scenes", "scenes": n_scenes, "n_range": [500, 16000], "dim": 3,
             "eps": 1e-3,
             "families": list(scenes.FAMILIES)}
@@ -222,7 +232,8 @@ def cpu_baseline(frames, offsets, dim, budget_s, per_step_budget=None, steps_exa
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    frames, offsets, eps, cfg = make_workload(args.workload, 0, max(4, args.frames), args.scenes)
+    frames, offsets, eps, cfg = make_workload(args.workload, 0, max(4, args.frames), args.scenes,
+                                              workers=args.gen_workers or min(16, os.cpu_count() or 1))
     dim = frames.shape[2]
     per_step = max(0.02, 120.0 / max(1, args.steps + args.warmup))
     cb, steps, el = cpu_baseline(frames, offsets, dim, budget_s=per_step * args.steps, per_step_budget=per_step,
@@ -252,26 +263,30 @@ def aggregate(ms, n_points, dist=None, device="cpu"):
     return float(t.item()), int(nt.item())
 
 
-def graph_loop(ctx, dev_frames, F, eps, strategy, K, use_graph, stream, torch):
-    """Time K steps from the start of the ping-pong cycle (state at frame 0);
-    the cycle (2F steps, even) is captured once as a CUDA graph and replayed.
+def capture_steps(ctx, dev_frames, F, eps, strategy, start, count, torch):
+    """One CUDA graph of ``count`` steps whose step k targets frame
+    cycle_index(start + k)."""
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for k in range(count):
+            ctx.step(dev_frames[cycle_index(start + k, F)], eps, strategy)
+    return g
+
+
+def graph_loop(ctx, dev_frames, F, eps, strategy, K, use_graph, stream, torch, start=0):
+    """Time K steps from clock ``start`` (the state sits at frame
+    cycle_index(start - 1), frame 0 for start = 0): step k targets frame
+    cycle_index(start + k).  The schedule repeats every 2F steps, so one graph
+    of 2F steps is captured and replayed, plus one graph for the remainder.
     Returns (ms, steps taken)."""
     C = 2 * F
     graphs = []
     if use_graph:
         full, rem = divmod(K, C)
         if full:
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
-                for k in range(C):
-                    ctx.step(dev_frames[cycle_index(k, F)], eps, strategy)
-            graphs.append((g, full))
+            graphs.append((capture_steps(ctx, dev_frames, F, eps, strategy, start, C, torch), full))
         if rem:
-            g2 = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g2):
-                for k in range(rem):
-                    ctx.step(dev_frames[cycle_index(k, F)], eps, strategy)
-            graphs.append((g2, 1))
+            graphs.append((capture_steps(ctx, dev_frames, F, eps, strategy, start, rem, torch), 1))
         torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -282,7 +297,7 @@ def graph_loop(ctx, dev_frames, F, eps, strategy, K, use_graph, stream, torch):
                 g.replay()
     else:
         for k in range(K):
-            ctx.step(dev_frames[cycle_index(k, F)], eps, strategy)
+            ctx.step(dev_frames[cycle_index(start + k, F)], eps, strategy)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1), K
@@ -417,12 +432,15 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--warmup", type=int, default=64)
+    ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "c1", "c2", "c3"])
     ap.add_argument("--strategy", default="auto",
                     choices=["auto", "incremental", "rebuild", "allpairs", "threshold"])
-    ap.add_argument("--frames", type=int, default=32)
+    ap.add_argument("--frames", type=int, default=100, help="pre-generated forward frames")
+    ap.add_argument("--gen-workers", type=int, default=0, help="processes generating the frames (0: host cores)")
+    ap.add_argument("--sustained-ms", type=float, default=500.0,
+                    help="length of the extra sustained replay (0: skip)")
     ap.add_argument("--scenes", type=int, default=512, help="scenes in the batched workload")
     ap.add_argument("--family", default=None, choices=list(scenes.FAMILIES), help="diagnostics: one family only")
     ap.add_argument("--cell-scale", type=float, default=0.0, help="search-grid cell side / reference d2 (0: default)")
@@ -467,7 +485,8 @@ def main():
 
     F = max(2, args.frames)
     C = 2 * F
-    frames, offsets, eps, cfg = make_workload(args.workload, rank, F, args.scenes, args.family)
+    workers = args.gen_workers or min(16, os.cpu_count() or 1)
+    frames, offsets, eps, cfg = make_workload(args.workload, rank, F, args.scenes, args.family, workers)
     if args.family:
         cfg = dict(cfg, families=[args.family])
     N, dim = frames.shape[1], frames.shape[2]
@@ -498,8 +517,9 @@ def main():
         ctx.load_selector(params, norm)
         sel_meta = json.loads(str(np.load(selector.WEIGHTS)["meta"]))
 
-    # warm-up: W eager steps (whole cycles), the autotuner on the next 8 frames, back to frame 0
-    W = int(math.ceil(max(3, args.warmup) / C) * C)
+    # warm-up: W eager steps forward from frame 0 (the autotuner's probe steps,
+    # below, run from a snapshot and leave the state where it was)
+    W = max(3, args.warmup)
     for _ in range(W):
         do_step()
     tuned = None
@@ -511,9 +531,9 @@ def main():
                                    scales)
         tuned = {"scales": list(scales), "ms": [float(x) for x in ms_sc], "best": best}
         del probe
-    to_cycle_start()
     torch.cuda.synchronize()
     ctx.sync(raise_on_status=False)
+    t_start = clock[0]
 
     # ---- the timed region: K steps of the chosen strategy
     K = args.steps
@@ -522,7 +542,7 @@ def main():
     time.sleep(0.3)
     if dist:
         dist.barrier()
-    ms, _ = graph_loop(ctx, dev_frames, F, eps, strat, K, use_graph, stream, torch)
+    ms, _ = graph_loop(ctx, dev_frames, F, eps, strat, K, use_graph, stream, torch, start=clock[0])
     clock[0] += K
     if dist:
         dist.barrier()
@@ -531,6 +551,44 @@ def main():
     assert int(res["n_missed"].sum()) == 0, "safety rule missed a failure"
     ms_max, n_all = aggregate(ms, N, dist, "cuda")
     value = n_all * K / (ms_max / 1e3)
+    fwd_steps = max(0, min(K, F - t_start))   # timed steps that moved forward, before any turn
+    motion = {"timed_from_frame": t_start, "forward_steps": fwd_steps, "turned_steps": K - fwd_steps,
+              "frames": F + 1}
+
+    # ---- the benchmark configuration as written: 100 forward steps from frame 0,
+    # one CUDA graph (replayed once untimed from a snapshot, then timed)
+    forward = None
+    if use_graph and F >= 100:
+        to_cycle_start()
+        torch.cuda.synchronize()
+        ctx.snapshot()
+        g100 = capture_steps(ctx, dev_frames, F, eps, strat, clock[0], 100, torch)
+        g100.replay()
+        ctx.restore()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g100.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clock[0] += 100
+        ms_f = e0.elapsed_time(e1)
+        r100, _ = ctx.sync(raise_on_status=False)
+        assert int(r100["n_missed"].sum()) == 0, "safety rule missed a failure"
+        ms_f, _ = aggregate(ms_f, N, dist, "cuda")
+        forward = {"value": n_all * 100 / (ms_f / 1e3), "ms_per_step": ms_f / 100, "steps": 100,
+                   "frames": "1..100, forward only, state from frame 0", "graph": "one graph of 100 steps"}
+        del g100
+
+    # ---- a longer replay of the same schedule (at least --sustained-ms of GPU time)
+    sustained = None
+    if use_graph and args.sustained_ms > 0:
+        Ks = int(math.ceil(args.sustained_ms / max(1e-6, ms_max / K) / C)) * C
+        ms_s, _ = graph_loop(ctx, dev_frames, F, eps, strat, Ks, use_graph, stream, torch, start=clock[0])
+        clock[0] += Ks
+        ms_s, _ = aggregate(ms_s, N, dist, "cuda")
+        sustained = {"value": n_all * Ks / (ms_s / 1e3), "ms_per_step": ms_s / Ks, "steps": Ks,
+                     "ms": ms_s}
     to_cycle_start()
 
     # ---- the same batch under each plain strategy, and the plain single-scene loops
@@ -653,12 +711,20 @@ def main():
     step_counts = {"frontier_frac": float(cnt[:, 0].mean() / N), "searched_frac": float(cnt[:, 1].mean() / N),
                    "failed_frac": float(cnt[:, 2].mean() / N)}
     traffic, traffic_src = None, None
+    fp_now = cert.cert_source_fingerprint("step_kernels")
     if dom == "search" and args.workload == "batched" and args.family is None and args.scenes == 512 and \
             strat in (cert.CERT_AUTO, cert.CERT_INCREMENTAL):
-        traffic = SEARCH_TRAFFIC_BATCHED
-        traffic_src = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_search launch, same workload"
+        if SEARCH_TRAFFIC["bytes"] is not None and SEARCH_TRAFFIC["fingerprint"] == fp_now:
+            traffic = SEARCH_TRAFFIC["bytes"]
+            traffic_src = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_search launch, same "
+                           f"workload, on step_kernels {SEARCH_TRAFFIC['fingerprint']} "
+                           f"(commit {SEARCH_TRAFFIC['commit']})")
+        else:
+            traffic_src = (f"null: no ncu capture of the running step kernels (fingerprint {fp_now}); "
+                           f"the last capture ran on {SEARCH_TRAFFIC['fingerprint']}")
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "traffic_source": traffic_src,
+                "kernel_fingerprint": fp_now,
                 "peak_source": peak_kind, "phases": per_phase}
 
     # ---- end to end through the public API with host buffers (pinned): every step
@@ -714,13 +780,13 @@ def main():
             cert.cert_allpairs(pts)
             torch.cuda.synchronize()
             ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 3
-            ea.record(stream)
-            for _ in range(reps):
+            reps, t_ms = 3, 0.0
+            for _ in range(reps):        # each call waits for its stream (it reads the status word)
+                ea.record(stream)
                 cert.cert_allpairs(pts)
-            eb.record(stream)
-            torch.cuda.synchronize()
-            t_ms = ea.elapsed_time(eb) / reps
+                eb.record(stream)
+                torch.cuda.synchronize()
+                t_ms += ea.elapsed_time(eb) / reps
             pairs = nap * (nap - 1)
             ops = allpairs["ops_per_pair"] * pairs / (t_ms * 1e-3)
             allpairs["rows"].append({"n": nap, "ms": t_ms, "gpairs_per_s": pairs / (t_ms * 1e-3) / 1e9,
@@ -735,7 +801,9 @@ def main():
         cfg = dict(cfg)
         cfg.update({"strategy": args.strategy, "graph": use_graph, "frames": F + 1,
                     "cell_scale": ctx.cell_scale(), "autotune": tuned,
-                    "motion": "ping-pong over pre-generated frames, every step <= eps",
+                    "motion": "pre-generated frames walked forward from frame 0 (warm-up, then the timed "
+                              "steps); past the last frame the walk turns back; every step <= eps",
+                    "warmup_requested": args.warmup,
                     "l2": "no flush: working set > 126 MB L2 (inputs larger than L2)",
                     "parallelism": f"scene-replicas x{world}"})
         if sel_meta is not None:
@@ -744,7 +812,8 @@ def main():
                 "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
-                "step_counts": step_counts, "compare": compare, "regret": regret, "frontier_rules": rules,
+                "step_counts": step_counts, "motion": motion, "forward_100": forward, "sustained": sustained,
+                "compare": compare, "regret": regret, "frontier_rules": rules,
                 "matched_pair": matched_pair, "knn": knn, "single_scene": single, "allpairs": allpairs,
                 "status": cert.STATUS_NAMES[rc] if 0 <= rc < len(cert.STATUS_NAMES) else rc}
         print(json.dumps(line), flush=True)

@@ -234,7 +234,12 @@ cert_status cert_distances(cert_ctx *ctx, float *d_d1, float *d_d2, void *stream
  * Table 2) of a single point set d_pos [n][dim] (n >= 3): for each query --
  * every point when d_queries is NULL, else the nq listed indices -- the top-2
  * over all j != query.  Outputs are caller device buffers of length n (or nq).
- * Uses library-managed scratch from the stream-ordered allocator. */
+ * Uses library-managed scratch from the stream-ordered allocator.  The call
+ * waits for its stream at the end and returns the status the kernels
+ * latched: CERT_EINVAL for a non-finite coordinate, CERT_ETIMEOUT when a
+ * bounded bulk-copy wait gave up (in both cases the outputs are not valid),
+ * CERT_OK otherwise.  Enqueued inside a stream capture, it cannot wait: it
+ * returns CERT_OK and the latched status is not read. */
 cert_status cert_allpairs(const float *d_pos, int64_t n, int32_t dim, const int32_t *d_queries,
                           int64_t nq, int32_t *d_nn, float *d_d1sq, float *d_d2sq, void *stream);
 
@@ -331,11 +336,17 @@ cert_status cert_profile_end(cert_ctx *ctx, float *h_ms, int32_t max_steps, int3
  *     cert_allpairs but no more than the array holds); every call with
  *     n = nq <= 838,000 fits.  A call that would not fit returns CERT_EINVAL
  *     with the required size in cert_last_error(NULL); nothing is enqueued.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - CUDA loads the library's device code into a context lazily, so the
+ *     array's 32 MiB are committed by the driver at the first call on each
+ *     device, and that first call can fail with out-of-memory (CERT_ECUDA).
+ *     A caller with a fixed memory budget makes one call at start-up, before
+ *     any stream capture.  Every call looks up the array's device address
+ *     (cudaGetSymbolAddress) with the caller's device current.
  *   - All calls share the array: calls whose work overlaps on the GPU (for
- *     example on two streams at once) race and must be serialised. */
+ *     example on two streams at once) race and must be serialised.
+ *   - Like cert_allpairs, the call waits for its stream at the end and
+ *     returns the latched status: CERT_EINVAL for a non-finite coordinate,
+ *     CERT_ETIMEOUT when a bounded bulk-copy wait gave up. */
 cert_status cert_allpairs_noalloc(const float *d_pos, int64_t n, int32_t dim, const int32_t *d_queries,
                                   int64_t nq, int32_t *d_nn, float *d_d1sq, float *d_d2sq, void *stream);
 
@@ -355,6 +366,15 @@ const char *cert_last_error(const cert_ctx *ctx);
 
 /* Library version string. */
 const char *cert_version(void);
+
+/* Source fingerprint of one translation unit of this build (no counterpart in
+ * the paper): the first 16 hex digits of the SHA-256 of the unit's source file
+ * and every header, computed by the build.  `unit` is the source's base name
+ * without extension ("step_kernels", "allpairs", "knn", "mlp", "api",
+ * "allpairs_noalloc").  A profiler measurement of a kernel is valid for the
+ * build whose fingerprint it was taken on.  Returns a static string, or NULL
+ * for an unknown unit. */
+const char *cert_source_fingerprint(const char *unit);
 
 #ifdef __cplusplus
 }

@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import concurrent.futures
 import glob
+import hashlib
 import os
 import subprocess
 import sys
@@ -31,6 +32,31 @@ def sources():
 def deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h"))
+
+
+def headers():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+                  glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")))
+
+
+def fingerprints() -> dict:
+    """Per translation unit: the first 16 hex digits of the SHA-256 of its
+    source and every header, in a fixed order.  The library reports them
+    (cert_source_fingerprint), so a measurement taken on one build of a kernel
+    can be told apart from the build that is running."""
+    hh = hashlib.sha256()
+    for h in headers():
+        hh.update(os.path.basename(h).encode() + b"\0" + open(h, "rb").read())
+    out = {}
+    for src in sources():
+        d = hh.copy()
+        d.update(os.path.basename(src).encode() + b"\0" + open(src, "rb").read())
+        out[os.path.splitext(os.path.basename(src))[0]] = d.hexdigest()[:16]
+    return out
+
+
+def fingerprint_defines() -> list:
+    return [f"-DCERT_FP_{unit.upper()}=\"{fp}\"" for unit, fp in sorted(fingerprints().items())]
 
 
 def stale(lib: str = LIB) -> bool:
@@ -55,7 +81,7 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
     if not force and not stale(lib):
         return lib
     nvcc = os.environ.get("NVCC", "nvcc")
-    extra = ["-DCERT_DEBUG_BOUNDS"] if debug else []
+    extra = (["-DCERT_DEBUG_BOUNDS"] if debug else []) + fingerprint_defines()
     srcs = sources()
     with tempfile.TemporaryDirectory(prefix="certbuild_") as tmp:
         objs = [os.path.join(tmp, os.path.basename(f) + ".o") for f in srcs]

@@ -93,7 +93,7 @@ EXPORTS = ["cert_knn_init", "cert_knn_step", "cert_knn_get_views", "cert_knn_syn
            "cert_knn_profile",
            "cert_init", "cert_step", "cert_step_host", "cert_step_host_stream", "cert_rebuild", "cert_get_views",
            "cert_sync_result", "cert_distances", "cert_allpairs", "cert_destroy", "cert_last_error",
-           "cert_version", "cert_profile_begin", "cert_profile_end",
+           "cert_version", "cert_source_fingerprint", "cert_profile_begin", "cert_profile_end",
            "cert_allpairs_noalloc", "cert_set_cell_scale", "cert_set_cell_quantile", "cert_get_cell_scale", "cert_autotune",
            "cert_snapshot", "cert_restore", "cert_get_features", "cert_selector_load",
            "cert_mlp_workspace_bytes", "cert_mlp_forward", "cert_mlp_grad", "cert_mlp_adam",
@@ -218,6 +218,15 @@ def _view(ptr, shape, typestr, owner):
 
 def cert_version() -> str:
     return lib().cert_version().decode()
+
+
+def cert_source_fingerprint(unit: str):
+    """Source fingerprint of one translation unit of the loaded library (None if unknown)."""
+    fn = lib().cert_source_fingerprint
+    fn.argtypes = [ctypes.c_char_p]
+    fn.restype = ctypes.c_char_p
+    r = fn(unit.encode())
+    return r.decode() if r is not None else None
 
 
 def cert_last_error(ctx=None) -> str:

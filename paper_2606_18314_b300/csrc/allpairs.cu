@@ -423,4 +423,34 @@ cudaError_t launch_pack(const float *pos, int n, int dim, float4 *out, uint32_t 
     return cudaGetLastError();
 }
 
+cudaError_t allpairs_status_read(const uint32_t *d_status, uint32_t *h_status, bool *read, cudaStream_t st)
+{
+    *read = false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
+    e = cudaMemcpyAsync(h_status, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *read = e == cudaSuccess;
+    return e;
+}
+
+cert_status allpairs_status_code(uint32_t st)
+{
+    const char *msg = nullptr;
+    cert_status code = CERT_OK;
+    if (st & ST_INDEX) {
+        code = CERT_EINTERNAL;
+        msg = "cert_allpairs: an internal index check failed (debug build)";
+    } else if (st & ST_TIMEOUT) {
+        code = CERT_ETIMEOUT;
+        msg = "cert_allpairs: a bounded bulk-copy wait gave up; the results are not valid";
+    } else if (st & ST_NONFINITE) {
+        code = CERT_EINVAL;
+        msg = "cert_allpairs: non-finite coordinate in the positions; the results are not valid";
+    }
+    if (msg) record_thread_error(msg);
+    return code;
+}
+
 }  // namespace certk

@@ -10,18 +10,23 @@
 // size, so a call allocates nothing.
 //
 // The array is a static __device__ symbol: every GPU that loads the library
-// holds kNoAllocScratchBytes of it until the process exits.  Host code cannot
-// use the symbol's name as a device address, so the first call on each device
-// resolves the address with cudaGetSymbolAddress (with that device current)
-// and caches it; that first call should come before any stream capture.
+// holds kNoAllocScratchBytes of it until the process exits.  CUDA loads a
+// module into a context lazily, so the array's memory is committed by the
+// driver when this module first loads on a device -- at the first call on
+// that device, in the address lookup below.  That first call can therefore
+// fail with out-of-memory (CERT_ECUDA); a caller with a fixed memory budget
+// makes it at start-up, and makes it before any stream capture.  Host code
+// cannot use the symbol's name as a device address, so every call looks the
+// address up with cudaGetSymbolAddress, with the caller's device current.
 // All calls share the one array and it keeps the last call's contents: the
 // status word is cleared on every call and every partial slot a call reads is
 // written by the same call.  Calls whose work overlaps on the GPU (two streams
-// at once) race on the array; serialise them.
+// at once) race on the array; serialise them.  The call waits for its stream
+// at the end and returns the status the kernels latched (a non-finite
+// coordinate, a bulk-copy wait that gave up).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "cert_internal.cuh"
 #include "cert_launch.h"
@@ -29,7 +34,6 @@
 namespace certk {
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;   // 32 MiB per device
-constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -38,24 +42,17 @@ __global__ void k_noalloc_write_params(SceneParams *dst, SceneParams v)
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
 }
 
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set-up on first use).
+// Device address of the scratch array in the current device's context.  It is
+// looked up on every call rather than cached per device ordinal: after a
+// cudaDeviceReset the module is loaded again into a new context, and an
+// address cached from the old one would no longer be mapped.  Once the module
+// is loaded the lookup is a table read.
 static cudaError_t noalloc_scratch(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -146,6 +143,9 @@ extern "C" cert_status cert_allpairs_noalloc(const float *d_pos, int64_t n, int3
     mo.d1sq = d_d1sq;
     mo.d2sq = d_d2sq;
     if (e == cudaSuccess) e = launch_allpairs_merge(ap, mo, nq, s);
+    uint32_t st = 0;
+    bool have_st = false;
+    if (e == cudaSuccess) e = allpairs_status_read(status, &st, &have_st, s);
     if (e != cudaSuccess) return noalloc_fail(CERT_ECUDA, cudaGetErrorString(e));
-    return CERT_OK;
+    return have_st ? allpairs_status_code(st) : CERT_OK;
 }

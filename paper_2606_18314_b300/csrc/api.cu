@@ -238,7 +238,40 @@ static cert_status run_full(cert_ctx *c, int mode, const float *pos_in, cudaStre
 
 extern "C" {
 
-const char *cert_version(void) { return "certmaint-b300 0.1 (sm_103a)"; }
+const char *cert_version(void) { return "certmaint-b300 0.2 (sm_103a)"; }
+
+// The build passes each translation unit's source fingerprint (build.py).
+#ifndef CERT_FP_STEP_KERNELS
+#define CERT_FP_STEP_KERNELS "unknown"
+#endif
+#ifndef CERT_FP_ALLPAIRS
+#define CERT_FP_ALLPAIRS "unknown"
+#endif
+#ifndef CERT_FP_KNN
+#define CERT_FP_KNN "unknown"
+#endif
+#ifndef CERT_FP_MLP
+#define CERT_FP_MLP "unknown"
+#endif
+#ifndef CERT_FP_API
+#define CERT_FP_API "unknown"
+#endif
+#ifndef CERT_FP_ALLPAIRS_NOALLOC
+#define CERT_FP_ALLPAIRS_NOALLOC "unknown"
+#endif
+
+const char *cert_source_fingerprint(const char *unit)
+{
+    if (!unit) return nullptr;
+    static const struct {
+        const char *name, *fp;
+    } table[] = {{"step_kernels", CERT_FP_STEP_KERNELS}, {"allpairs", CERT_FP_ALLPAIRS},
+                 {"knn", CERT_FP_KNN},                   {"mlp", CERT_FP_MLP},
+                 {"api", CERT_FP_API},                   {"allpairs_noalloc", CERT_FP_ALLPAIRS_NOALLOC}};
+    for (const auto &t : table)
+        if (std::strcmp(unit, t.name) == 0) return t.fp;
+    return nullptr;
+}
 
 const char *cert_last_error(const cert_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
@@ -1002,8 +1035,11 @@ extern "C" cert_status cert_allpairs(const float *d_pos, int64_t n, int32_t dim,
     mo.d1sq = d_d1sq;
     mo.d2sq = d_d2sq;
     if (e == cudaSuccess) e = launch_allpairs_merge(ap, mo, nq, s);
+    uint32_t st = 0;
+    bool have_st = false;
+    if (e == cudaSuccess) e = allpairs_status_read(status, &st, &have_st, s);   // before the free below
     cudaError_t e2 = cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(nullptr, "cert_allpairs launch", e);
     if (e2 != cudaSuccess) return cuda_fail(nullptr, "cudaFreeAsync", e2);
-    return CERT_OK;
+    return have_st ? allpairs_status_code(st) : CERT_OK;
 }

@@ -110,6 +110,13 @@ int allpairs_chunks_for(long long qblocks, long long n, int dim, int cap);
 cudaError_t launch_allpairs_merge(const APArgs &a, const APMergeOut &o, long long n_queries_total,
                                   cudaStream_t st);
 cudaError_t launch_pack(const float *pos, int n, int dim, float4 *out, uint32_t *status, cudaStream_t st);
+// Wait for the all-pairs work on st and copy its latched status word to *h_status
+// (*read = true).  A stream under capture cannot be waited on: then nothing is
+// read (*read = false) and the capture is left intact.
+cudaError_t allpairs_status_read(const uint32_t *d_status, uint32_t *h_status, bool *read, cudaStream_t st);
+// cert_status of latched status bits: a failed debug check, a wait that gave up,
+// a non-finite coordinate, in this order of precedence; CERT_OK for none.
+cert_status allpairs_status_code(uint32_t st);
 
 // Sets the text cert_last_error(NULL) returns on the calling thread.
 void record_thread_error(const char *msg);

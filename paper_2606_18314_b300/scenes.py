@@ -404,3 +404,26 @@ class BatchMotion:
         for k in range(count):
             out[k + 1] = self.advance()
         return out
+
+    def frames_parallel(self, count: int, workers: int) -> np.ndarray:
+        """The array ``frames(count)`` returns for scenes still at their
+        first frame, generated scene by scene in a pool of spawned processes.
+        Each scene's stream depends only on its own seed, so the result is
+        the same; the scenes themselves are left untouched."""
+        if any(m.t != 0 for m in self.scenes):
+            raise ValueError("frames_parallel needs every scene at its first frame")
+        import concurrent.futures
+        import multiprocessing
+        tot, off = int(self.offsets[-1]), self.offsets
+        out = np.empty((count + 1, tot, self.dim), np.float32)
+        jobs = [(m.family, m.n, m.dim, m.eps, m.seed, m.steps, m.jitter, count) for m in self.scenes]
+        with concurrent.futures.ProcessPoolExecutor(max_workers=max(1, workers),
+                                                    mp_context=multiprocessing.get_context("spawn")) as ex:
+            for s, fr in enumerate(ex.map(_scene_frames, jobs, chunksize=max(1, len(jobs) // (4 * max(1, workers))))):
+                out[:, off[s]:off[s + 1]] = fr
+        return out
+
+
+def _scene_frames(job):
+    family, n, dim, eps, seed, steps, jitter, count = job
+    return Motion(family, n, dim, eps, seed=seed, steps=steps, jitter=jitter).frames(count)

@@ -147,3 +147,14 @@ def test_debug_variant_loads_and_exports_every_symbol():
     env = dict(os.environ, CERT_LIB_VARIANT="debug")
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0 and "ok" in out.stdout, out.stderr[-2000:]
+
+
+def test_source_fingerprints_match_the_build(L):
+    """The library reports the fingerprint of the sources it was built from,
+    unit by unit, so a profiler measurement can name the build it belongs to."""
+    from paper_2606_18314_b300 import cert
+    fps = cbuild.fingerprints()
+    assert "step_kernels" in fps and "allpairs" in fps
+    for unit, fp in fps.items():
+        assert cert.cert_source_fingerprint(unit) == fp, unit
+    assert cert.cert_source_fingerprint("no_such_unit") is None

@@ -94,6 +94,24 @@ def test_allpairs_ties_and_duplicates(torch, dim):
     assert_cert_equal({"nn": nn, "d1sq": d1, "d2sq": d2}, ref, tag="ties")
 
 
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_allpairs_reports_a_non_finite_coordinate(torch, bad):
+    """k_pack latches a non-finite coordinate; cert_allpairs waits for its
+    stream, reads the status word and returns CERT_EINVAL (the results are not
+    valid), and a following call on finite input is clean again."""
+    from paper_2606_18314_b300 import cert
+    rng = np.random.default_rng(77)
+    pts = rng.random((3000, 3)).astype(np.float32)
+    pts[1234, 1] = bad
+    with pytest.raises(cert.CertError) as ei:
+        cert.cert_allpairs(dev(torch, pts))
+    assert ei.value.code == cert.CERT_EINVAL
+    assert "non-finite" in str(ei.value)
+    pts[1234, 1] = 0.5
+    nn, d1, d2 = cert.cert_allpairs(dev(torch, pts))
+    assert_cert_equal({"nn": nn, "d1sq": d1, "d2sq": d2}, oracle.top2(pts), tag="after a rejected call")
+
+
 def test_allpairs_query_list(torch):
     from paper_2606_18314_b300 import cert
     rng = np.random.default_rng(9)

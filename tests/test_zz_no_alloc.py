@@ -63,3 +63,27 @@ def test_noalloc_rejects_sizes_beyond_its_array():
         cert.cert_allpairs_noalloc(p)
     assert ei.value.code == cert.CERT_EINVAL
     assert "scratch" in str(ei.value)
+
+
+def test_noalloc_reports_a_non_finite_coordinate():
+    """A NaN coordinate made on the host is latched in the static array's
+    status word; the call waits for its stream, reads the word and returns
+    CERT_EINVAL, as cert_allpairs does.  The word is cleared by the next call,
+    whose results are exact again."""
+    import torch
+    from paper_2606_18314_b300 import build, cert
+    build.build()
+    rng = np.random.default_rng(31)
+    pts = rng.random((2000, 3)).astype(np.float32)
+    pts[17, 2] = np.nan
+    p = torch.from_numpy(pts).cuda()
+    for fn in (cert.cert_allpairs, cert.cert_allpairs_noalloc):
+        with pytest.raises(cert.CertError) as ei:
+            fn(p)
+        assert ei.value.code == cert.CERT_EINVAL
+    pts[17, 2] = 0.25
+    got = cert.cert_allpairs_noalloc(torch.from_numpy(pts).cuda())
+    o = oracle.top2(pts)
+    assert np.array_equal(got[0].cpu().numpy(), o.nn)
+    assert np.array_equal(got[1].cpu().numpy().view(np.uint32), o.d1sq.view(np.uint32))
+    assert np.array_equal(got[2].cpu().numpy().view(np.uint32), o.d2sq.view(np.uint32))
