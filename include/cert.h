@@ -253,6 +253,32 @@ cert_status cert_set_cell_scale(cert_ctx *ctx, float scale);
 cert_status cert_set_cell_quantile(cert_ctx *ctx, float quantile);
 float cert_get_cell_scale(const cert_ctx *ctx);
 
+/* How cert_step runs a step (no counterpart in the paper, which runs one
+ * scene's phases as separate GPU passes):
+ *   CERT_PATH_MULTI  one kernel per phase over every scene of the batch
+ *                    (seven launches and a clear per step; any size);
+ *   CERT_PATH_FUSED  one launch per step, one CTA per scene running every
+ *                    phase, counters and histograms in shared memory; for
+ *                    scenes of at most 16,384 points and 16,384 search-grid
+ *                    buckets (next_pow2(n) x bucket_factor), and for every
+ *                    strategy but CERT_ALLPAIRS (which always takes the
+ *                    multi-kernel path);
+ *   CERT_PATH_AUTO   (default) the fused step when no scene has more than
+ *                    4,096 points or search-grid buckets -- such a scene's
+ *                    sorted points and bucket starts then stay in shared
+ *                    memory for the whole step -- else the multi-kernel step
+ *                    (one CTA per larger scene is slower than spreading each
+ *                    phase over the GPU).
+ * Both paths give the same results bit for bit (every certificate, flag,
+ * count and H), except n_searched, which counts the work the refresh left to
+ * the search.  cert_set_step_path returns CERT_EINVAL for CERT_PATH_FUSED on a
+ * context whose scenes exceed the limits.  Takes effect from the next step. */
+typedef enum { CERT_PATH_AUTO = 0, CERT_PATH_MULTI = 1, CERT_PATH_FUSED = 2 } cert_step_path;
+cert_status cert_set_step_path(cert_ctx *ctx, int32_t path);
+/* The path the next cert_step with this strategy takes (CERT_PATH_MULTI or
+ * CERT_PATH_FUSED; -1 for a NULL context). */
+int32_t cert_get_step_path(const cert_ctx *ctx, int32_t strategy);
+
 /* Autotuner (the grid cell side of Sec. 2's uniform grid, chosen by timing):
  * for each of the n_scales candidate scales, restore the current state, run
  * one step on frame 0 (it builds the grid at that scale) and time steps on
@@ -311,13 +337,15 @@ cert_status cert_mlp_adam(float *d_params, const float *d_grad, float *d_m, floa
                           float beta1, float beta2, float eps, void *stream);
 
 /* Number of timed phases per step (see cert_profile_end). */
-#define CERT_N_PHASES 7
+#define CERT_N_PHASES 8
 
 /* Diagnostics: while enabled, cert_step records a CUDA event on its stream
  * before the first and after every phase of the next max_steps steps
  * (phases: 0 clear accumulators, 1 prepare, 2 scans, 3 select, 4 scatter and
  * refresh -- or all-pairs tiles, 5 grid search -- or all-pairs merge,
- * 6 finalize).  Creates the events here, so the timed steps allocate nothing. */
+ * 6 finalize; 7 the fused step, whose one launch runs every phase and leaves
+ * phases 0-6 empty, as a multi-kernel step leaves phase 7 empty).  Creates
+ * the events here, so the timed steps allocate nothing. */
 cert_status cert_profile_begin(cert_ctx *ctx, int32_t max_steps);
 
 /* Stop recording, wait for the recorded steps and write h_ms[step][phase]
@@ -370,8 +398,8 @@ const char *cert_version(void);
 /* Source fingerprint of one translation unit of this build (no counterpart in
  * the paper): the first 16 hex digits of the SHA-256 of the unit's source file
  * and every header, computed by the build.  `unit` is the source's base name
- * without extension ("step_kernels", "allpairs", "knn", "mlp", "api",
- * "allpairs_noalloc").  A profiler measurement of a kernel is valid for the
+ * without extension ("step_kernels", "fused_step", "allpairs", "knn", "mlp",
+ * "api", "allpairs_noalloc").  A profiler measurement of a kernel is valid for the
  * build whose fingerprint it was taken on.  Returns a static string, or NULL
  * for an unknown unit. */
 const char *cert_source_fingerprint(const char *unit);

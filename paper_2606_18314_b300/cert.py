@@ -97,12 +97,14 @@ EXPORTS = ["cert_knn_init", "cert_knn_step", "cert_knn_get_views", "cert_knn_syn
            "cert_allpairs_noalloc", "cert_set_cell_scale", "cert_set_cell_quantile", "cert_get_cell_scale", "cert_autotune",
            "cert_snapshot", "cert_restore", "cert_get_features", "cert_selector_load",
            "cert_mlp_workspace_bytes", "cert_mlp_forward", "cert_mlp_grad", "cert_mlp_adam",
-           "cert_selftest_bounded_wait"]
+           "cert_selftest_bounded_wait", "cert_set_step_path", "cert_get_step_path"]
 MLP_PARAMS = 4866
 CERT_FRONTIER_STEP, CERT_FRONTIER_POINT, CERT_FRONTIER_CLOCK = 0, 1, 2
 FRONTIER_RULE = {"step": CERT_FRONTIER_STEP, "point": CERT_FRONTIER_POINT, "clock": CERT_FRONTIER_CLOCK}
-N_PHASES = 7
-PHASE_NAMES = ["clear", "prepare", "scan", "select", "scatter_refresh", "search", "finalize"]
+N_PHASES = 8
+PHASE_NAMES = ["clear", "prepare", "scan", "select", "scatter_refresh", "search", "finalize", "fused"]
+CERT_PATH_AUTO, CERT_PATH_MULTI, CERT_PATH_FUSED = 0, 1, 2
+STEP_PATH = {"auto": CERT_PATH_AUTO, "multi": CERT_PATH_MULTI, "fused": CERT_PATH_FUSED}
 
 
 def lib():
@@ -337,7 +339,7 @@ class Context:
     """
 
     def __init__(self, pos, offsets=None, cell_scale=0.0, policy=CERT_INCREMENTAL, stream=None,
-                 bucket_factor=0, cell_quantile=0.0, frontier_rule="step", audit=()):
+                 bucket_factor=0, cell_quantile=0.0, frontier_rule="step", audit=(), path="auto"):
         import torch
         self.dim = int(pos.shape[1])
         self._keep = []
@@ -365,6 +367,24 @@ class Context:
                                _stream_ptr(stream)))
         self.h = h
         self.device = pos.device
+        if path != "auto":
+            self.set_step_path(path)
+
+    def set_step_path(self, path):
+        """cert_set_step_path: "auto", "multi" (one kernel per phase) or "fused" (one launch per step)."""
+        fn = lib().cert_set_step_path
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        fn.restype = ctypes.c_int
+        _check(fn(self.h, STEP_PATH[path] if isinstance(path, str) else int(path)), self.h)
+
+    def step_path(self, strategy=CERT_INCREMENTAL):
+        """The path ("multi" or "fused") the next step with this strategy takes."""
+        fn = lib().cert_get_step_path
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+        fn.restype = ctypes.c_int32
+        if isinstance(strategy, str):
+            strategy = STRATEGY[strategy]
+        return {CERT_PATH_MULTI: "multi", CERT_PATH_FUSED: "fused"}[fn(self.h, int(strategy))]
 
     def close(self):
         if getattr(self, "h", None):

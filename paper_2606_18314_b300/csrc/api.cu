@@ -80,6 +80,11 @@ struct cert_ctx {
     } step_graph[4];
     cudaStream_t capture_stream = nullptr;
     uint64_t settings_epoch = 1;
+    // fused step (one launch per step): eligibility, the path setting, the CTA order (largest scene first)
+    bool fused_ok = false;
+    int step_path = CERT_PATH_AUTO;
+    int max_n = 0, max_T = 0;
+    int32_t *order = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
     size_t snap_bytes = 0;
     int snap_cur = 0;
@@ -215,6 +220,29 @@ static StepArgs make_args(cert_ctx *c, int mode)
     return a;
 }
 
+// The fused step (one launch per step, fused_step.cu) runs a step when every
+// scene fits its limits, the strategy is not the all-pairs pass, and either it
+// was asked for or, on CERT_PATH_AUTO, every scene is small enough to keep its
+// sorted points in shared memory.  For larger scenes one CTA per scene is a
+// long chain of dependent L2 accesses on one SM, slower than the multi-kernel
+// step that spreads each phase over the GPU (measured: N = 16,000, d = 3,
+// 0.30 vs 0.067 ms per step; the 512-scene batch 1.38 vs 0.65 ms).
+static bool fused_resident(const cert_ctx *c)
+{
+    return c->max_n <= kFusedResMaxN && c->max_T <= kFusedResMaxN;
+}
+
+static bool use_fused(const cert_ctx *c, int strategy)
+{
+    if (!c->fused_ok || strategy == STRAT_ALL || c->step_path == CERT_PATH_MULTI) return false;
+    if (c->step_path == CERT_PATH_FUSED) return true;
+    return fused_resident(c);
+}
+
+// CTA size of the fused step: 512 threads (two CTAs per SM) for batches that
+// fill the GPU, 1024 for fewer scenes than SMs (more threads per scene).
+static int fused_block(const cert_ctx *c) { return c->S >= 148 ? 512 : 1024; }
+
 // Grid build + full search of every point of the current positions
 // (initial certificates and cert_rebuild).
 static cert_status run_full(cert_ctx *c, int mode, const float *pos_in, cudaStream_t s)
@@ -259,6 +287,9 @@ const char *cert_version(void) { return "certmaint-b300 0.2 (sm_103a)"; }
 #ifndef CERT_FP_ALLPAIRS_NOALLOC
 #define CERT_FP_ALLPAIRS_NOALLOC "unknown"
 #endif
+#ifndef CERT_FP_FUSED_STEP
+#define CERT_FP_FUSED_STEP "unknown"
+#endif
 
 const char *cert_source_fingerprint(const char *unit)
 {
@@ -267,7 +298,8 @@ const char *cert_source_fingerprint(const char *unit)
         const char *name, *fp;
     } table[] = {{"step_kernels", CERT_FP_STEP_KERNELS}, {"allpairs", CERT_FP_ALLPAIRS},
                  {"knn", CERT_FP_KNN},                   {"mlp", CERT_FP_MLP},
-                 {"api", CERT_FP_API},                   {"allpairs_noalloc", CERT_FP_ALLPAIRS_NOALLOC}};
+                 {"api", CERT_FP_API},                   {"allpairs_noalloc", CERT_FP_ALLPAIRS_NOALLOC},
+                 {"fused_step", CERT_FP_FUSED_STEP}};
     for (const auto &t : table)
         if (std::strcmp(unit, t.name) == 0) return t.fp;
     return nullptr;
@@ -351,6 +383,14 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
             for (int qb = 0; qb < nqb; ++qb) items.push_back({k, qb, ch, 0});
     }
     c->n_quads = quads;
+    c->fused_ok = true;
+    for (int k = 0; k < c->S; ++k) {
+        const SceneParams &p = c->h_sp[k];
+        const int64_t cells = (int64_t)std::pow((double)p.g_h, (double)c->dim) + 0.5;
+        c->max_n = std::max(c->max_n, (int)p.n);
+        c->max_T = std::max(c->max_T, (int)p.bucket_mask + 1);
+        if (p.n > kFusedMaxN || p.bucket_mask + 1 > kFusedMaxBuckets || cells > kFusedMaxHCells) c->fused_ok = false;
+    }
     c->n_buckets = (int)boff;
     c->n_buckets_pad = (int)ceil_div(boff + 1, kScanTile) * kScanTile;
     c->ntiles_b = c->n_buckets_pad / kScanTile;
@@ -371,11 +411,11 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_inF = cv.take<uint8_t>(Npad), o_failed = cv.take<uint8_t>(Npad),
                  o_sflag = cv.take<uint8_t>(Npad), o_brank = cv.take<int2>(N), o_sorted = cv.take<float4>(4 * c->n_quads),
                  o_bstart = cv.take<int32_t>(c->n_buckets_pad), o_far = cv.take<int32_t>(N),
-                 o_nlogn = cv.take<double>(kNlognTable),
+                 o_nlogn = cv.take<double>(kLogTables * kNlognTable),
                  o_stage = cv.take<float>(N * c->dim), o_stage2 = cv.take<float>(N * c->dim), o_items = cv.take<APItem>(items.size()),
                  o_pd = cv.take<float>(3 * apoff), o_pj = cv.take<int32_t>(3 * apoff),
                  o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16), o_feat = cv.take<float>(S * 8),
-                 o_resring = cv.take<cert_scene_result>(2 * S);
+                 o_resring = cv.take<cert_scene_result>(2 * S), o_order = cv.take<int32_t>(S);
     const int64_t Nclk = (c->frontier_rule == CERT_FRONTIER_CLOCK) ? N : 0;
     const size_t o_clks = cv.take<double>(Nclk), o_clkc = cv.take<float>(Nclk), o_clkg = cv.take<float>(Nclk);
     cv.off = (cv.off + 255) & ~size_t(255);
@@ -427,6 +467,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->sel_params = (float *)(b + o_selp);
     c->sel_norm = (float *)(b + o_seln);
     c->feat = (float *)(b + o_feat);
+    c->order = (int32_t *)(b + o_order);
     if (Nclk) {
         c->clk_s = (double *)(b + o_clks);
         c->clk_c = (float *)(b + o_clkc);
@@ -446,9 +487,17 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     std::vector<int32_t> scene_of(N);
     for (int k = 0; k < c->S; ++k)
         for (int64_t i = off[k]; i < off[k + 1]; ++i) scene_of[i] = k;
-    std::vector<double> nlogn(kNlognTable);
-    nlogn[0] = 0.0;
-    for (int k = 1; k < kNlognTable; ++k) nlogn[k] = (double)k * std::log((double)k);
+    // FP64 tables (cert_internal.cuh): k ln k, ln k, 1/k, 1/ln k, and k ln k in fixed point
+    std::vector<double> nlogn(size_t(kLogTables) * kNlognTable, 0.0);
+    for (int k = 1; k < kNlognTable; ++k) {
+        const double lk = std::log((double)k);
+        nlogn[k] = (double)k * lk;
+        nlogn[size_t(kNlognTable) + k] = lk;
+        nlogn[size_t(2) * kNlognTable + k] = 1.0 / (double)k;
+        nlogn[size_t(3) * kNlognTable + k] = k >= 2 ? 1.0 / lk : 0.0;
+        const long long fx = std::llround(std::ldexp((double)k * (long double)lk, kNlognFixBits));
+        std::memcpy(&nlogn[size_t(4) * kNlognTable + k], &fx, sizeof(fx));
+    }
     std::vector<SceneState> st0(S);
     for (int k = 0; k < c->S; ++k) {
         std::memset(&st0[k], 0, sizeof(SceneState));
@@ -465,8 +514,14 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     up(c->sp, c->h_sp.data(), S * sizeof(SceneParams));
     up(c->st, st0.data(), S * sizeof(SceneState));
     up(c->scene_of, scene_of.data(), N * sizeof(int32_t));
-    up(c->nlogn, nlogn.data(), kNlognTable * sizeof(double));
+    up(c->nlogn, nlogn.data(), nlogn.size() * sizeof(double));
     up(c->ap_items, items.data(), items.size() * sizeof(APItem));
+    // fused steps launch the largest scenes first (ties by index)
+    std::vector<int32_t> order(S);
+    for (int k = 0; k < c->S; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return c->h_sp[x].n > c->h_sp[y].n; });
+    up(c->order, order.data(), S * sizeof(int32_t));
     if (rc == CERT_OK) {
         // padding bytes of the flag arrays and the result block start at zero
         cudaError_t e3 = cudaMemsetAsync(c->inF, 0, Npad, s);
@@ -510,6 +565,17 @@ cert_status cert_step(cert_ctx *c, const float *d_pos_new, float eps, int32_t st
     cudaEvent_t *ev = nullptr;
     if (c->prof_on && c->prof_n < c->prof_max) ev = &c->prof_ev[size_t(c->prof_n++) * (CERT_N_PHASES + 1)];
     auto mark = [&](int k) -> cudaError_t { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
+    if (use_fused(c, strategy)) {
+        // one launch: every phase of every scene (phases 0-6 of the profile are empty)
+        for (int k = 0; k <= 7; ++k) CK(c, mark(k));
+        CK(c, launch_fused_step(a, c->order, fused_block(c), fused_resident(c), s));
+        CK(c, mark(8));
+        c->cur ^= 1;
+        c->last = s;
+        c->stepped = true;
+        if (out) cert_get_views(c, out);
+        return CERT_OK;
+    }
     CK(c, mark(0));
     CK(c, cudaMemsetAsync(c->zero, 0, c->zero_bytes, s));
     CK(c, mark(1));
@@ -546,6 +612,7 @@ cert_status cert_step(cert_ctx *c, const float *d_pos_new, float eps, int32_t st
     CK(c, mark(6));
     CK(c, launch_step_phase(a, PH_FINALIZE, s));
     CK(c, mark(7));
+    CK(c, mark(8));
     c->cur ^= 1;
     c->last = s;
     c->stepped = true;
@@ -766,6 +833,23 @@ cert_status cert_set_cell_scale(cert_ctx *c, float scale)
 }
 
 float cert_get_cell_scale(const cert_ctx *c) { return c ? c->cell_scale : 0.0f; }
+
+cert_status cert_set_step_path(cert_ctx *c, int32_t path)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    if (path < CERT_PATH_AUTO || path > CERT_PATH_FUSED) return fail(c, CERT_EINVAL, "unknown step path");
+    if (path == CERT_PATH_FUSED && !c->fused_ok)
+        return fail(c, CERT_EINVAL, "a scene exceeds the fused step's limits (16,384 points, 16,384 search-grid buckets)");
+    c->step_path = path;
+    ++c->settings_epoch;
+    return CERT_OK;
+}
+
+int32_t cert_get_step_path(const cert_ctx *c, int32_t strategy)
+{
+    if (!c) return -1;
+    return use_fused(c, strategy) ? CERT_PATH_FUSED : CERT_PATH_MULTI;
+}
 
 cert_status cert_set_cell_quantile(cert_ctx *c, float q)
 {

@@ -22,7 +22,9 @@ constexpr int kMedianSample = 1024;                    // points sampled for the
 constexpr int kMaxSearchRes = 2048;                    // search-grid cells per axis, cap
 constexpr int kMaxExtend = 16;                         // face extensions before a warp scans the scene
 constexpr uint32_t kSpinLimit = 1u << 22;              // bounded device waits
-constexpr int kNlognTable = 1 << 16;                   // k ln k table entries (FP64)
+constexpr int kNlognTable = 1 << 16;                   // entries of each FP64 table below
+constexpr int kLogTables = 5;                           // k ln k, ln k, 1/k, 1/ln k, k ln k fixed point
+constexpr int kNlognFixBits = 40;                       // k ln k as round(k ln k * 2^40) in an int64
 
 // Latched device status bits (returned by cert_sync_result).
 enum : uint32_t { ST_TIMEOUT = 1u, ST_NONFINITE = 2u, ST_EBOUND = 4u, ST_INDEX = 8u };
@@ -380,6 +382,19 @@ __device__ __forceinline__ float eps_of(const SceneAcc *acc, int s)
     return __fsqrt_rn(__uint_as_float(acc[s].eps_bits));
 }
 
+// The host-computed FP64 tables, kNlognTable entries each, back to back:
+// k ln k, ln k, 1/k, 1/ln k (0 for k < 2), and k ln k in fixed point.  FP64 logarithms and divisions
+// are slow on this part; a lookup replaces each of them on the device.
+__device__ __forceinline__ double tab_ln(const double *tab, int k) { return tab[kNlognTable + k]; }
+__device__ __forceinline__ double tab_inv(const double *tab, int k) { return tab[2 * kNlognTable + k]; }
+__device__ __forceinline__ double tab_inv_ln(const double *tab, int k) { return tab[3 * kNlognTable + k]; }
+// k ln k in fixed point (kNlognFixBits fraction bits): sums of these are exact and
+// order-independent, and any sum over a scene's cells stays below 2^58.
+__device__ __forceinline__ long long tab_nlogn_fix(const double *tab, int k)
+{
+    return reinterpret_cast<const long long *>(tab + 4 * kNlognTable)[k];
+}
+
 // n ln n increment when a histogram count goes old -> old + 1 (FP64).
 __device__ __forceinline__ double nlogn_step(const double *tab, int old)
 {
@@ -456,10 +471,13 @@ __device__ __forceinline__ double run_sum_f64(unsigned mask, double v)
 
 // ----------------------------------------------------------------------------- block scan
 
-// Exclusive scan of one value per thread across a 256-thread block; returns
-// the exclusive prefix, and the block total through *total.
+// Exclusive scan of one value per thread across a block of NT threads (a
+// multiple of 32, at most 1024); returns the exclusive prefix, and the block
+// total through *total.  smem_warp holds NT / 32 words.
+template <int NT = kThreads>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total, uint32_t *smem_warp)
 {
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps, at most 32 of them");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -470,17 +488,17 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *t
     if (lane == 31) smem_warp[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = (lane < kThreads / 32) ? smem_warp[lane] : 0u;
+        uint32_t w = (lane < NT / 32) ? smem_warp[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(kFull, w, o);
             if (lane >= o) w += y;
         }
-        if (lane < kThreads / 32) smem_warp[lane] = w;  // inclusive warp prefixes
+        if (lane < NT / 32) smem_warp[lane] = w;  // inclusive warp prefixes
     }
     __syncthreads();
     const uint32_t warp_base = warp ? smem_warp[warp - 1] : 0u;
-    *total = smem_warp[kThreads / 32 - 1];
+    *total = smem_warp[NT / 32 - 1];
     return warp_base + x - v;
 }
 

@@ -64,6 +64,26 @@ struct StepArgs {
 };
 
 cudaError_t launch_step_phase(const StepArgs &a, int phase, cudaStream_t st);
+
+// ---------------------------------------------------------------- fused step
+
+// Limits of the fused step (one CTA runs every phase of one scene, counters in
+// shared memory; fused_step.cu): points per scene, search-grid buckets per
+// scene (16-bit counters), entropy-grid cells per scene (26^3), row-range
+// table entries per thread.
+constexpr int kFusedMaxN = 16384;
+constexpr int kFusedMaxBuckets = 16384;
+constexpr int kFusedMaxHCells = 17576;
+constexpr int kFusedRows = 9;
+// Scenes of at most this many points keep their sorted points and bucket
+// starts in shared memory during a fused step.
+constexpr int kFusedResMaxN = 4096;
+// One step of every scene (MODE_STEP, any strategy but all-pairs) in one
+// launch: CTA b runs scene order[b] (order may be NULL: scene b), block =
+// 512 or 1024 threads.  resident: every scene has at most kFusedResMaxN points
+// and search-grid buckets, so its sorted points and bucket starts are kept in
+// shared memory (1024 threads; block is ignored).
+cudaError_t launch_fused_step(const StepArgs &a, const int32_t *order, int block, bool resident, cudaStream_t st);
 cudaError_t launch_distances(const float *d1sq, const float *d2sq, float *d1, float *d2, int n,
                              cudaStream_t st);
 

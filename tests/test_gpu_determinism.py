@@ -29,9 +29,11 @@ def _run(torch, frames, offsets, strategies, audit):
         ctx.step(torch.from_numpy(frames[t]).cuda(), 2e-3, strat)
         res, _ = ctx.sync()
         v = ctx.views()
-        nf = int(res["n_frontier"].sum())
+        fr = v["frontier"].cpu().numpy()
+        lists = np.concatenate([fr[int(res["frontier_start"][s]):int(res["frontier_start"][s]) + int(res["n_frontier"][s])]
+                                for s in range(len(res))])
         outs.append((res.copy(), {k: v[k].cpu().numpy().copy() for k in ("nn", "d1sq", "d2sq", "cell", "failed")},
-                     v["frontier"][:nf].cpu().numpy().copy()))
+                     lists))
     ctx.close()
     return outs
 

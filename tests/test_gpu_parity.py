@@ -1,5 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle, element
-by element on the same seeded inputs.  Bit-exact for nn, d1^2, d2^2, cells,
+by element on the same seeded inputs, on both step paths (one kernel per
+phase, and one launch per step).  Bit-exact for nn, d1^2, d2^2, cells,
 frontier membership and order, failure marks and every count; H and H_cand
 within 1e-6 absolute of the oracle's FP64 value (the tolerance of the
 certificate-maintenance target)."""
@@ -25,6 +26,23 @@ def torch():
     from paper_2606_18314_b300 import build
     build.build()
     return t
+
+
+@pytest.fixture(params=["multi", "fused"], autouse=True)
+def step_path(request, monkeypatch):
+    """Every test of this module runs on both step paths: one kernel per phase
+    ("multi") and one launch per step ("fused").  Contexts take the path as
+    their default; the all-pairs tests, which build no context, simply run
+    twice."""
+    from paper_2606_18314_b300 import cert
+    init = cert.Context.__init__
+
+    def init_with_path(self, *args, **kw):
+        kw.setdefault("path", request.param)
+        init(self, *args, **kw)
+
+    monkeypatch.setattr(cert.Context, "__init__", init_with_path)
+    return request.param
 
 
 def dev(torch, a):
@@ -272,8 +290,12 @@ def test_strategies_agree_bitwise(torch):
             ctx.step(dev(torch, frames[t]), 2e-3, strat)
         res, _ = ctx.sync()
         v = ctx.views()
+        fr = host(v["frontier"])
+        # each scene's list sits at its frontier_start (the fused step places it at the
+        # scene's first point, the multi-kernel step packs the lists back to back)
         outs[strat] = [host(v[k]).copy() for k in ("nn", "d1sq", "d2sq", "failed", "cell")] + [
-            host(v["frontier"])[:int(res["n_frontier"].sum())].copy()]
+            fr[int(res["frontier_start"][s]):int(res["frontier_start"][s]) + int(res["n_frontier"][s])].copy()
+            for s in range(len(res))]
         ctx.close()
     for strat in ["rebuild", "allpairs"]:
         for a, b in zip(outs["incremental"], outs[strat]):
