@@ -96,6 +96,7 @@ struct cert_ctx {
     uint32_t *tile_ctr = nullptr;
     uint64_t *tstat_b = nullptr, *tstat_p = nullptr;
     int32_t *bucket_count = nullptr, *hocc = nullptr, *hfail = nullptr, *hcand = nullptr;
+    uint32_t *mgrid = nullptr, *mdil = nullptr;   // motion grid (zeroed every step) and its dilation
     cudaStream_t last = nullptr;
     bool stepped = false;
     // phase profiling (diagnostics)
@@ -179,6 +180,8 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.acc = c->acc;
     a.status = c->status;
     a.bucket_count = c->bucket_count;
+    a.mgrid = c->mgrid;
+    a.mdil = c->mdil;
     a.bucket_start = c->bucket_start;
     a.brank = c->brank;
     a.squad = c->squad;
@@ -415,7 +418,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_stage = cv.take<float>(N * c->dim), o_stage2 = cv.take<float>(N * c->dim), o_items = cv.take<APItem>(items.size()),
                  o_pd = cv.take<float>(3 * apoff), o_pj = cv.take<int32_t>(3 * apoff),
                  o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16), o_feat = cv.take<float>(S * 8),
-                 o_resring = cv.take<cert_scene_result>(2 * S), o_order = cv.take<int32_t>(S);
+                 o_resring = cv.take<cert_scene_result>(2 * S), o_order = cv.take<int32_t>(S),
+                 o_mdil = cv.take<uint32_t>(S * kMotionStride);
     const int64_t Nclk = (c->frontier_rule == CERT_FRONTIER_CLOCK) ? N : 0;
     const size_t o_clks = cv.take<double>(Nclk), o_clkc = cv.take<float>(Nclk), o_clkg = cv.take<float>(Nclk);
     cv.off = (cv.off + 255) & ~size_t(255);
@@ -423,7 +427,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     const size_t o_acc = cv.take<SceneAcc>(S), o_ctr = cv.take<uint32_t>(4), o_farc = cv.take<int32_t>(4),
                  o_tb = cv.take<uint64_t>(c->ntiles_b), o_tp = cv.take<uint64_t>(c->ntiles_p),
                  o_bcount = cv.take<int32_t>(c->n_buckets_pad), o_hocc = cv.take<int32_t>(hoff),
-                 o_hfail = cv.take<int32_t>(hoff), o_hcand = cv.take<int32_t>(hoff);
+                 o_hfail = cv.take<int32_t>(hoff), o_hcand = cv.take<int32_t>(hoff),
+                 o_mgrid = cv.take<uint32_t>(S * kMotionStride);
     c->zero_bytes = cv.off - zero_begin;
     c->blob_bytes = cv.off;
     cudaError_t e = cudaMalloc((void **)&c->blob, c->blob_bytes);
@@ -468,6 +473,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->sel_norm = (float *)(b + o_seln);
     c->feat = (float *)(b + o_feat);
     c->order = (int32_t *)(b + o_order);
+    c->mdil = (uint32_t *)(b + o_mdil);
+    c->mgrid = (uint32_t *)(b + o_mgrid);
     if (Nclk) {
         c->clk_s = (double *)(b + o_clks);
         c->clk_c = (float *)(b + o_clkc);

@@ -26,6 +26,19 @@ constexpr int kNlognTable = 1 << 16;                   // entries of each FP64 t
 constexpr int kLogTables = 5;                           // k ln k, ln k, 1/k, 1/ln k, k ln k fixed point
 constexpr int kNlognFixBits = 40;                       // k ln k as round(k ln k * 2^40) in an int64
 
+// Motion grid: a coarse per-scene grid of kMotionRes<DIM> cells per axis (a
+// power of two, so cell coordinates and cell faces are exact in FP32) holding
+// the largest squared displacement of the step's points in each cell, and its
+// dilation by one cell (the largest over the 3^d block around each cell).
+// kMotionStride cells are reserved per scene.
+constexpr int kMotionStride = 512;
+template <int DIM>
+struct MotionRes {
+    static constexpr int R = (DIM == 3) ? 8 : 16;
+    static constexpr int cells = (DIM == 3) ? R * R * R : R * R;
+};
+static_assert(MotionRes<3>::cells <= kMotionStride && MotionRes<2>::cells <= kMotionStride, "motion grid stride");
+
 // Latched device status bits (returned by cert_sync_result).
 enum : uint32_t { ST_TIMEOUT = 1u, ST_NONFINITE = 2u, ST_EBOUND = 4u, ST_INDEX = 8u };
 
@@ -260,7 +273,81 @@ __device__ __forceinline__ int cell_coord(float x, int g, float gf)
     return (int)floorf(t);
 }
 
-// Bucket of the first cell of row (cy, cz) of the search grid; the cells of a
+// Motion-grid cell of a position: floor(x * R) per axis clamped to [0, R-1];
+// R is a power of two, so x * R is exact.
+template <int DIM>
+__device__ __forceinline__ int motion_cell(const float4 p)
+{
+    constexpr int R = MotionRes<DIM>::R;
+    const int mx = cell_coord(p.x, R, (float)R);
+    const int my = cell_coord(p.y, R, (float)R);
+    if (DIM == 2) return my * R + mx;
+    return (cell_coord(p.z, R, (float)R) * R + my) * R + mx;
+}
+
+// Dilation of a scene's motion grid: dst[c] = max of src over the cells of the
+// 3^d block around c (clamped to the grid), as one pass per axis (a max over
+// a box is the composition of the max over its three edges).  t0 and t1 are
+// shared-memory scratch of MotionRes<DIM>::cells words each; src and dst may
+// be global or shared.  Called by all nt threads of the block (it holds
+// barriers); thread tid produces cells tid, tid + nt, ...
+template <int DIM>
+__device__ __forceinline__ void dilate_motion(const uint32_t *src, uint32_t *t0, uint32_t *t1, uint32_t *dst,
+                                              int tid, int nt)
+{
+    constexpr int R = MotionRes<DIM>::R, C = MotionRes<DIM>::cells;
+    // axis 0 (x, stride 1): src -> t0
+    for (int c = tid; c < C; c += nt) {
+        const int x = c % R;
+        uint32_t m = src[c];
+        if (x > 0) m = max(m, src[c - 1]);
+        if (x < R - 1) m = max(m, src[c + 1]);
+        t0[c] = m;
+    }
+    __syncthreads();
+    // axis 1 (y, stride R): t0 -> t1 (2-D: -> dst)
+    uint32_t *d1 = (DIM == 3) ? t1 : dst;
+    for (int c = tid; c < C; c += nt) {
+        const int y = (c / R) % R;
+        uint32_t m = t0[c];
+        if (y > 0) m = max(m, t0[c - R]);
+        if (y < R - 1) m = max(m, t0[c + R]);
+        d1[c] = m;
+    }
+    if (DIM == 3) {
+        __syncthreads();
+        // axis 2 (z, stride R^2): t1 -> dst
+        for (int c = tid; c < C; c += nt) {
+            const int z = c / (R * R);
+            uint32_t m = t1[c];
+            if (z > 0) m = max(m, t1[c - R * R]);
+            if (z < R - 1) m = max(m, t1[c + R * R]);
+            dst[c] = m;
+        }
+    }
+}
+
+// Distance from p to the nearest face of the 3^d motion-grid block around its
+// cell that is not on the grid edge (rounded down; +inf when every face is on
+// the edge).  A point outside the block is at least this far from p: its cell
+// lies beyond one of those faces (edge cells are clamped, nothing lies beyond).
+template <int DIM>
+__device__ __forceinline__ float motion_block_face(const float4 p)
+{
+    constexpr int R = MotionRes<DIM>::R;
+    constexpr float inv = 1.0f / (float)R;   // exact: R is a power of two
+    float f = __int_as_float(0x7f800000);
+    const float c[3] = {p.x, p.y, p.z};
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const int m = cell_coord(c[k], R, (float)R);
+        if (m - 1 > 0) f = fminf(f, __fsub_rd(c[k], (float)(m - 1) * inv));
+        if (m + 1 < R - 1) f = fminf(f, __fsub_rd((float)(m + 2) * inv, c[k]));
+    }
+    return f;
+}
+
+// Latched device status bits; the cells of a
 // row occupy consecutive buckets (mod T).  When the whole grid fits in the
 // bucket table (g^dim <= T) the mapping is the plain linear cell index and
 // buckets never mix cells; otherwise the row is placed by a 32-bit integer

@@ -34,6 +34,8 @@ struct StepArgs {
     int32_t *bucket_start;         // [n_buckets_pad]
     int2 *brank;                   // [n] (bucket, rank in bucket)
     float4 *squad;                 // points in bucket order, quad layout (sorted_store), padded per scene
+    uint32_t *mgrid;               // [n_scenes][kMotionStride] max squared displacement per motion cell (bits)
+    uint32_t *mdil;                // [n_scenes][kMotionStride] its dilation by one cell
     uint8_t *sflag;                // [n_pad] by sorted slot: 1 = search this point
     int32_t *far_list;             // [n] sorted slots left to the far pass
     int32_t *far_count;            // number of entries in far_list (zeroed every call)

@@ -284,17 +284,23 @@ __device__ int select_scene(const StepArgs &a, int s, float eps, int nF, double 
 // O(1) refresh of point i (an addition to the paper's record:
 // every certificate is exact each step, Cor. A.2).  Every point other than
 // the three stored candidates was at least L away; a step changes the
-// distance from i to any j by at most |p'_i - p_i| + eps_t (triangle
-// inequality, as in Lemma 1), so L minus that bounds the next step.  The
-// fresh keys of the three candidates are sorted; when the second is closer
-// than the shrunk bound, the first two keys are the exact top-2 and the
-// certificate is written (a change of nn is a failure: *changed = 1).
+// distance from i to any j by at most |p'_i - p_i| + |p'_j - p_j| (triangle
+// inequality, as in Lemma 1), so L minus a bound on that bounds the next
+// step.  The bound is tried twice: first with eps_t for |p'_j - p_j| (the
+// scene's largest step), then, if that fails, with the largest step among the
+// points of the 3^d motion-grid block around p'_i (mdil: the scene's dilated
+// motion grid), a bound that holds for every point inside the block, capped
+// by the distance to the block's faces, which bounds every point outside it.
+// The fresh keys of the three candidates are sorted; when the second is
+// closer than the shrunk bound, the first two keys are the exact top-2 and
+// the certificate is written (a change of nn is a failure: *changed = 1).
 // Otherwise the point needs a search, and L[i] receives its box hint (the
 // second fresh key's distance: the fresh runner-up over all points is no
 // farther).  Returns true when the point needs a search.
 template <int DIM>
 __device__ __forceinline__ bool refresh_point(const StepArgs &a, const SceneParams &sp, float eps, int i, float4 p,
-                                              int na, int nb, int nc, float Lold, bool inc, int *changed)
+                                              int na, int nb, int nc, float Lold, bool inc, const uint32_t *mdil,
+                                              int *changed)
 {
     *changed = 0;
     float hint = 0.0f;             // no box hint unless the candidates are valid
@@ -323,12 +329,24 @@ __device__ __forceinline__ bool refresh_point(const StepArgs &a, const ScenePara
         }
         // any distance from i changed by at most |p'_i - p_i| + eps_t
         // (triangle inequality); both terms rounded up with slack
-        const float shrink = __fmul_ru(__fadd_ru(__fsqrt_ru(p.w), eps), 1.0f + 0x1p-18f);
-        const float Lnew = __fsub_rd(Lold, shrink);
+        const float own = __fsqrt_ru(p.w);
+        const float shrink = __fmul_ru(__fadd_ru(own, eps), 1.0f + 0x1p-18f);
+        float Lnew = __fsub_rd(Lold, shrink);
         hint = __fsqrt_ru(d2);
+        const float d2g = __fmul_ru(d2, 1.0f + 0x1p-19f);
+        bool ok = inc && Lnew > 0.0f && d2g < __fmul_rd(Lnew, Lnew);
+        if (inc && !ok) {
+            // the local bound: the points of the motion block moved at most
+            // sqrt(mdil) each; the points outside it are beyond its faces
+            const float dl = __fsqrt_ru(__uint_as_float(mdil[motion_cell<DIM>(p)]));
+            const float sl = __fmul_ru(__fadd_ru(own, dl), 1.0f + 0x1p-18f);
+            const float Lloc = fminf(__fsub_rd(Lold, sl), motion_block_face<DIM>(p));
+            if (Lloc > Lnew) Lnew = Lloc;
+            ok = Lnew > 0.0f && d2g < __fmul_rd(Lnew, Lnew);
+        }
         // every point outside {nn, nn2, nn3} is now at least Lnew away, so
         // when the second key is closer the top-2 is the first two keys
-        if (inc && Lnew > 0.0f && __fmul_ru(d2, 1.0f + 0x1p-19f) < __fmul_rd(Lnew, Lnew)) {
+        if (ok) {
             need = false;
             a.nn[i] = j1;
             a.nn2[i] = j2;

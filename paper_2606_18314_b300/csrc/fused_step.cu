@@ -58,7 +58,8 @@ struct FusedLayout {
     static constexpr int kHcell = kStart + kStartBytes;                           // RES: entropy cell per point
     static constexpr int kHcellBytes = RES ? MAXN * 2 : 0;
     static constexpr int kMisc = kHcell + kHcellBytes;
-    static constexpr int kBytes = kMisc + 2048;
+    static constexpr int kMotion = kMisc + 2048;                                  // motion grid, its dilation
+    static constexpr int kBytes = kMotion + 3 * kMotionStride * 4;
 };
 
 constexpr int kFixCache = 64;   // fixed-point k ln k entries cached in shared memory
@@ -151,6 +152,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fused_step(const StepArgs a, 
     float4 *s_quad = reinterpret_cast<float4 *>(smem + Lay::kQuads);    // RES
     int32_t *s_start = reinterpret_cast<int32_t *>(smem + Lay::kStart); // RES
     uint16_t *s_hcell = reinterpret_cast<uint16_t *>(smem + Lay::kHcell); // RES: entropy cell (< 4096)
+    uint32_t *s_mgrid = reinterpret_cast<uint32_t *>(smem + Lay::kMotion);  // motion grid
+    uint32_t *s_mdil = s_mgrid + kMotionStride;                            // ... dilated
+    uint32_t *s_mtmp = s_mdil + kMotionStride;                             // ... scratch of the dilation
 
     const int s = order ? order[blockIdx.x] : (int)blockIdx.x;
     const SceneParams sp = a.sp[s];
@@ -166,6 +170,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fused_step(const StepArgs a, 
     for (int k = tid; k < (T + 1) / 2; k += NT) cnt[k] = 0u;
     for (int k = tid; k < (hcells + 1) / 2; k += NT) hist[k] = 0u;
     for (int k = tid; k < MAXN / 32; k += NT) flag[k] = 0u;
+    for (int k = tid; k < MotionRes<DIM>::cells; k += NT) s_mgrid[k] = 0u;
     for (int k = tid; k < kFixCache; k += NT) m.fix[k] = tab_nlogn_fix(a.nlogn, k);
     if (RES && tid < 16) {
         // the last quad's padding slots: NaN coordinates, index -1 (all-ones bits)
@@ -200,6 +205,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fused_step(const StepArgs a, 
             const int cz = (DIM == 3) ? cell_coord(p.z, g, gf) : 0;
             const int b = (int)((row_base<DIM>(cy, cz, g, dense) + (uint32_t)cx) & (uint32_t)sp.bucket_mask);
             const int rank = smem_inc_u16(cnt, b);
+            if (D > 0.0f) atomicMax(&s_mgrid[motion_cell<DIM>(p)], __float_as_uint(D));
             a.brank[i] = make_int2(sp.bucket_off + b, rank);
             const int hx = cell_coord(p.x, sp.g_h, ghf);
             const int hy = cell_coord(p.y, sp.g_h, ghf);
@@ -234,6 +240,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fused_step(const StepArgs a, 
             run += smem_get_u16(cnt, b);
         }
         if (RES && tid == 0) s_start[T] = off + n;
+        // the refresh's local motion bound (s_mgrid serves as the second scratch)
+        dilate_motion<DIM>(s_mgrid, s_mtmp, s_mgrid, s_mdil, tid, NT);
     }
     for (int k = tid; k < (hcells + 1) / 2; k += NT) hist[k] = 0u;   // occupancy done: frontier cells next
     __syncthreads();
@@ -296,7 +304,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fused_step(const StepArgs a, 
         else
             sorted_store(a.squad, slot - off + sp.s_off, p.x, p.y, p.z, i);
         int changed = 0;
-        const bool need = refresh_point<DIM>(a, sp, eps, i, p, a.nn[i], a.nn2[i], a.nn3[i], a.L[i], inc, &changed);
+        const bool need =
+            refresh_point<DIM>(a, sp, eps, i, p, a.nn[i], a.nn2[i], a.nn3[i], a.L[i], inc, s_mdil, &changed);
         if (need) atomicOr(&flag[(slot - off) >> 5], 1u << ((slot - off) & 31));
         if (changed) {
             const uint32_t fl = a.inF[i];
@@ -505,6 +514,8 @@ template <int DIM, int NT, int MAXN>
 static cudaError_t launch_fused_dim(const StepArgs &a, const int32_t *order, cudaStream_t st)
 {
     constexpr int bytes = FusedLayout<NT, MAXN>::kBytes;
+    // per CTA at most 227 KB; CTAs per SM (1024 / NT) x (bytes + 1 KB reserved) within the SM's 228 KB
+    static_assert(bytes <= 227 * 1024 && (1024 / NT) * (bytes + 1024) <= 228 * 1024, "fused step shared memory");
     // a host-side attribute of the function (not a stream operation): set on every launch,
     // so that each device the library launches on has it
     const cudaError_t e =

@@ -96,6 +96,13 @@ __global__ void __launch_bounds__(kThreads, 5) k_prepare(const StepArgs a)   // 
         const bool dense = grid_is_dense<DIM>(g, sp.bucket_mask + 1);
         b[k] = sp.bucket_off + (int)((row_base<DIM>(cy, cz, g, dense) + (uint32_t)cx) & (uint32_t)sp.bucket_mask);
         rank[k] = atomicAdd(&a.bucket_count[b[k]], 1);
+        // the motion grid of the refresh's local bound (static points add nothing)
+        // (read first: cells of dense scenes take hundreds of points, and their
+        // maximum is reached early, so most of the atomics would serialise for nothing)
+        if (dbits[k]) {
+            uint32_t *mc = &a.mgrid[s[k] * kMotionStride + motion_cell<DIM>(p[k])];
+            if (dbits[k] > __ldcg(mc)) atomicMax(mc, dbits[k]);
+        }
         // entropy grid on the post-step position (Def. 2)
         if (a.mode != MODE_REBUILD) {
             const int gh = sp.g_h;
@@ -332,10 +339,14 @@ template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
 {
     __shared__ SelectSmem sm;
+    __shared__ uint32_t s_mot[2][kMotionStride];
     const int s = blockIdx.x;
     const SceneAcc &acc = a.acc[s];
     const int nF = a.fstart[s + 1] - a.fstart[s];
     select_scene<DIM, kThreads>(a, s, eps_of(a.acc, s), nF, acc.s_front, acc.occ, acc.frontier_cells, sm);
+    if (a.mode == MODE_STEP)   // the refresh's local motion bound (k_scatter_refresh)
+        dilate_motion<DIM>(a.mgrid + s * kMotionStride, s_mot[0], s_mot[1], a.mdil + s * kMotionStride,
+                           threadIdx.x, kThreads);
 }
 
 // ============================================================================ k_scatter_refresh
@@ -390,7 +401,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
         bool need = true;
         if (step) {
             need = refresh_point<DIM>(a, sp, eps_of(a.acc, s[k]), i, p[k], na[k], nb[k], nc[k], Lold[k],
-                                      a.st[s[k]].strategy == STRAT_INC, &changed[k]);
+                                      a.st[s[k]].strategy == STRAT_INC, a.mdil + s[k] * kMotionStride,
+                                      &changed[k]);
             if (changed[k]) {
                 const uint32_t fl = a.inF[i];
                 missed[k] = !(fl & 1u);
