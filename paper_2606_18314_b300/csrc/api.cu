@@ -226,10 +226,18 @@ static StepArgs make_args(cert_ctx *c, int mode)
 // The fused step (one launch per step, fused_step.cu) runs a step when every
 // scene fits its limits, the strategy is not the all-pairs pass, and either it
 // was asked for or, on CERT_PATH_AUTO, every scene is small enough to keep its
-// sorted points in shared memory.  For larger scenes one CTA per scene is a
-// long chain of dependent L2 accesses on one SM, slower than the multi-kernel
-// step that spreads each phase over the GPU (measured: N = 16,000, d = 3,
-// 0.30 vs 0.067 ms per step; the 512-scene batch 1.38 vs 0.65 ms).
+// sorted points in shared memory -- and, for fewer than kFusedAutoScenes
+// scenes, has at most kFusedAutoSingleN points.  For larger scenes one CTA per
+// scene is a long chain of dependent L2 accesses on one SM, slower than the
+// multi-kernel step that spreads each phase over the GPU (measured: N =
+// 16,000, d = 3, 0.29 vs 0.051 ms per step; the 512-scene batch 1.38 vs
+// 0.65 ms).  A lone scene crosses over between 2,000 and 4,000 points (d = 2:
+// 0.033 vs 0.041 ms at 2,000, 0.056 vs 0.041 ms at 4,000; d = 3: 0.040 vs
+// 0.044 and 0.058 vs 0.046 ms), while batches of 16 or more scenes of at most
+// 4,096 points gain from the fused step at every size measured (512 scenes of
+// 500 to 4,000 points, d = 3: 0.21 vs 0.29 ms).
+constexpr int kFusedAutoScenes = 16;
+constexpr int kFusedAutoSingleN = 2560;
 static bool fused_resident(const cert_ctx *c)
 {
     return c->max_n <= kFusedResMaxN && c->max_T <= kFusedResMaxN;
@@ -239,7 +247,7 @@ static bool use_fused(const cert_ctx *c, int strategy)
 {
     if (!c->fused_ok || strategy == STRAT_ALL || c->step_path == CERT_PATH_MULTI) return false;
     if (c->step_path == CERT_PATH_FUSED) return true;
-    return fused_resident(c);
+    return fused_resident(c) && (c->S >= kFusedAutoScenes || c->max_n <= kFusedAutoSingleN);
 }
 
 // CTA size of the fused step: 512 threads (two CTAs per SM) for batches that

@@ -31,6 +31,8 @@
 // repaired by a search.  The test is independent of the safety rule, so a
 // frontier point it proves is repaired in O(1) too (a change of nn is then
 // found by the reordering of {nn, nn2}).
+#include <algorithm>
+
 #include "cert_phases.cuh"
 
 namespace certk {
@@ -439,24 +441,31 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
 
 // One CTA compacts the flagged slots of CHUNK consecutive sorted slots
 // (ascending, so a warp's queries are neighbours and share most rows), then
-// searches them kThreads at a time.  CHUNK is kSearchChunk; a grid that fits
-// one wave even at half that (a small or single scene) takes half-size chunks,
-// so that a CTA's queries fit one round of kThreads instead of spilling a few
-// stragglers into a second round on the critical path.
-template <int DIM, int CHUNK>
+// searches them kThreads / G at a time, G lanes per query.  CHUNK is
+// kSearchChunk with G = 1; a grid that fits one wave even at half that (a
+// small or single scene) takes half-size chunks, so that a CTA's queries fit
+// one round of kThreads instead of spilling a few stragglers into a second
+// round on the critical path.  A grid that fits one wave at 64 slots per CTA
+// (a scene of at most about 38,000 points) takes 64-slot chunks with G = 4
+// lanes per query: the GPU has lanes to spare there, and each lane walks a
+// quarter of its query's quads, which cuts the chain of dependent loads that
+// bounds a lone query's latency.
+template <int DIM, int CHUNK, int G>
 __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 64 registers: 4 CTAs per SM
 {
     constexpr int NR = (DIM == 3) ? 9 : 3;
-    constexpr int PER = CHUNK / kThreads;   // slots per thread in the compaction
+    constexpr int NQ = kThreads / G;                       // queries per round
+    constexpr int PER = CHUNK >= kThreads ? CHUNK / kThreads : 1;   // slots per thread in the compaction
     static_assert(PER == 1 || PER == 2 || PER == 4, "the flag load below reads one, two or four flags at once");
+    static_assert(CHUNK >= kThreads || G * CHUNK <= kThreads, "a chunk of queries fits one round");
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ int s_list[CHUNK];
-    __shared__ int2 s_rng[(kMaxRows > NR ? kMaxRows : NR) * kThreads];   // per-thread row ranges, column-major
+    __shared__ int2 s_rng[(kMaxRows > NR ? kMaxRows : NR) * NQ];   // per-query row ranges, column-major
     const int base = blockIdx.x * CHUNK + threadIdx.x * PER;
     // flags beyond n_total are zero up to the padded length (a multiple of the
     // scan tile, itself a multiple of CHUNK); each flag byte is 0 or 1
     uint32_t fw = 0u;
-    if (base < a.n_total)
+    if (base < a.n_total && threadIdx.x * PER < CHUNK)
         fw = (PER == 4)   ? *reinterpret_cast<const uint32_t *>(a.sflag + base)
              : (PER == 2) ? (uint32_t)*reinterpret_cast<const uint16_t *>(a.sflag + base)
                           : (uint32_t)a.sflag[base];
@@ -467,10 +476,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
         if ((fw >> (8 * u)) & 0xffu) s_list[pre++] = base + u;
     __syncthreads();
 
-    for (int r0 = 0; r0 < (int)count; r0 += kThreads) {
-        if (r0 + (int)(threadIdx.x & ~31u) >= (int)count) break;  // whole idle warps leave together
-        const int e = r0 + (int)threadIdx.x;
-        const bool active = e < (int)count;
+    const int gl = (G > 1) ? (int)(threadIdx.x % G) : 0;   // lane within the query's group
+    for (int r0 = 0; r0 < (int)count; r0 += NQ) {
+        if (r0 + (int)(threadIdx.x & ~31u) / G >= (int)count) break;  // whole idle warps leave together
+        const int e = r0 + (int)threadIdx.x / G;
+        const bool active = e < (int)count;   // the same for the G lanes of a group
         int s = -1;
         SearchOut o = {0, 0, 0, 0, 0.0};
         if (active) {
@@ -507,16 +517,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
             Top4 t;
             float L;
             const float hint = (a.mode == MODE_STEP) ? a.L[gi] : 0.0f;   // written by the refresh
-            if (grid_search<DIM>(c, t, L, s_rng + threadIdx.x, hint))
-                o = write_certificate(a, sp, gi, t, L,
-                                      [&](int hc) { return atomicAdd(&a.hfail[sp.h_off + hc], 1); });
-            else
-                a.far_list[atomicAdd(a.far_count, 1)] = slot;   // finished by k_far
+            const bool ok = grid_search<DIM, NQ, kMaxRows, G>(c, t, L, s_rng + threadIdx.x / G, hint, gl);
+            if (gl == 0) {   // the group's lanes hold the same result; one writes it
+                if (ok)
+                    o = write_certificate(a, sp, gi, t, L,
+                                          [&](int hc) { return atomicAdd(&a.hfail[sp.h_off + hc], 1); });
+                else
+                    a.far_list[atomicAdd(a.far_count, 1)] = slot;   // finished by k_far
+            }
         }
         if (a.mode == MODE_STEP) {
             // slots of one scene are contiguous, so lanes form contiguous scene runs
             const unsigned m = scene_run_mask(s);
-            const int nsr = run_sum_i32(m, active ? 1 : 0);
+            const int nsr = run_sum_i32(m, (active && gl == 0) ? 1 : 0);
             const int nc = run_sum_i32(m, o.changed);
             const int nm = run_sum_i32(m, o.missed);
             const int fc = run_sum_i32(m, o.first);
@@ -692,13 +705,19 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
             k_scatter_refresh<DIM, kScatPer><<<nblk(a.n_total, kThreads * kScatPer), kThreads, 0, st>>>(a);
         break;
     case PH_SEARCH:
-        if (nblk(a.n_total, kSearchChunk / 4) <= kSearchSmallGrid)
-            k_search<DIM, kSearchChunk / 4><<<nblk(a.n_total, kSearchChunk / 4), kThreads, 0, st>>>(a);
+        if (nblk(a.n_total, kThreads / 8) <= kSearchSmallGrid)
+            k_search<DIM, kThreads / 8, 8><<<nblk(a.n_total, kThreads / 8), kThreads, 0, st>>>(a);
+        else if (nblk(a.n_total, kThreads / 4) <= kSearchSmallGrid)
+            k_search<DIM, kThreads / 4, 4><<<nblk(a.n_total, kThreads / 4), kThreads, 0, st>>>(a);
+        else if (nblk(a.n_total, kSearchChunk / 4) <= kSearchSmallGrid)
+            k_search<DIM, kSearchChunk / 4, 1><<<nblk(a.n_total, kSearchChunk / 4), kThreads, 0, st>>>(a);
         else if (nblk(a.n_total, kSearchChunk / 2) <= kSearchSmallGrid)
-            k_search<DIM, kSearchChunk / 2><<<nblk(a.n_total, kSearchChunk / 2), kThreads, 0, st>>>(a);
+            k_search<DIM, kSearchChunk / 2, 1><<<nblk(a.n_total, kSearchChunk / 2), kThreads, 0, st>>>(a);
         else
-            k_search<DIM, kSearchChunk><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
-        if (cudaPeekAtLastError() == cudaSuccess) k_far<DIM><<<kFarCtas, kThreads, 0, st>>>(a);
+            k_search<DIM, kSearchChunk, 1><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
+        // far queries are rare: a small grid gets a few CTAs (each scans a whole scene per query)
+        if (cudaPeekAtLastError() == cudaSuccess)
+            k_far<DIM><<<std::min(kFarCtas, std::max(8, nblk(a.n_total, 4096))), kThreads, 0, st>>>(a);
         break;
     case PH_FINALIZE:
         if (a.mode == MODE_STEP && (a.audit & CERT_AUDIT_GEOMETRY))

@@ -1,9 +1,10 @@
 """GPU: single scenes on both sides of every size at which the step changes
 its launch shape.  The certificates must be the same on either side.
 
-* k_search takes 256 sorted slots per CTA while ceil(N / 256) <= 4 x 148,
-  then 512 while ceil(N / 512) <= 4 x 148, then 1024: N = 151,552 | 151,553
-  and 303,104 | 303,105.
+* k_search takes 64 sorted slots per CTA with four lanes per query while
+  ceil(N / 64) <= 4 x 148, then 256 slots with one lane per query while
+  ceil(N / 256) <= 4 x 148, then 512 while ceil(N / 512) <= 4 x 148, then
+  1024: N = 37,888 | 37,889, 151,552 | 151,553 and 303,104 | 303,105.
 * k_scan issues in latency order while the scan grid (bucket tiles + point
   tiles of 2048) has fewer than 3 x 148 tiles.  At d = 3 with N in
   (262,144, 524,288] there are 257 bucket tiles, so the switch is at
@@ -35,8 +36,8 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("n", [151552, 151553, 189440, 189441, 227328, 227329, 303104, 303105, 378880, 378881,
-                               380928, 380929])
+@pytest.mark.parametrize("n", [37888, 37889, 151552, 151553, 189440, 189441, 227328, 227329, 303104, 303105,
+                               378880, 378881, 380928, 380929])
 def test_both_sides_of_each_launch_shape_switch(torch, n):
     from paper_2606_18314_b300 import cert
     m = scenes.Motion("uniform_brownian", n, 3, 1e-3, seed=n, steps=8)

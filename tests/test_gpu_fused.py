@@ -184,3 +184,20 @@ def test_fused_geometry_audit_matches_oracle(torch):
             assert abs(float(res[s]["compactness"]) - r.compactness) <= GEOM_TOL
             refs[s] = r.cert
     ctx.close()
+
+
+def test_auto_path_rule(torch):
+    """CERT_PATH_AUTO: a lone scene takes the fused step up to 2,560 points;
+    16 or more scenes do while none has more than 4,096 points; larger scenes
+    take the multi-kernel step."""
+    from paper_2606_18314_b300 import cert
+    rng = np.random.default_rng(3)
+    for n, want in ((2560, "fused"), (2561, "multi"), (4096, "multi")):
+        c = cert.Context(torch.from_numpy(rng.random((n, 3)).astype(np.float32)).cuda())
+        assert c.step_path("incremental") == want, n
+        c.close()
+    for sizes, want in (([4096] * 16, "fused"), ([4096] * 15, "multi"), ([500] * 15 + [4097], "multi")):
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        c = cert.Context(torch.from_numpy(rng.random((int(off[-1]), 3)).astype(np.float32)).cuda(), offsets=off)
+        assert c.step_path("incremental") == want, (len(sizes), max(sizes))
+        c.close()
