@@ -460,6 +460,8 @@ def main():
     ap.add_argument("--knn-steps", type=int, default=240,
                     help="graph-replayed steps per k-nearest-neighbour case (0: skip)")
     ap.add_argument("--compare-steps", type=int, default=256)
+    ap.add_argument("--flip-steps", type=int, default=64,
+                    help="steps per variant of the per-family strategy flips inside the batch (0: skip)")
     ap.add_argument("--single-steps", type=int, default=256,
                     help="graph-replayed steps per single-scene configuration (0 to skip)")
     ap.add_argument("--no-compare", action="store_true")
@@ -642,6 +644,34 @@ def main():
         regret["reference"] = "per step min(incremental, rebuild) on identical state, CUDA events"
         to_cycle_start()
 
+    # ---- what each scene family's choice costs inside the batch: the family's scenes
+    # forced to rebuild (the rest incremental) against every scene incremental, each
+    # timed over the same cycle of frames from its start (per-scene policy, no selector)
+    flips = None
+    if args.flip_steps > 0 and args.workload == "batched" and args.family is None:
+        fam_of = np.arange(S) % len(scenes.FAMILIES)
+        if sel_meta is not None:
+            ctx.load_selector(None, None)
+        Kf = args.flip_steps
+        variants = [("all_incremental", np.full(S, cert.CERT_INCREMENTAL))]
+        variants += [(f"{scenes.FAMILIES[f]}_rebuild",
+                      np.where(fam_of == f, cert.CERT_REBUILD, cert.CERT_INCREMENTAL)) for f in range(len(scenes.FAMILIES))]
+        ms_flip = {}
+        for name, pol in variants:
+            ctx.set_scene_policy(pol)
+            to_cycle_start(cert.CERT_AUTO)
+            msf, _ = graph_loop(ctx, dev_frames, F, eps, cert.CERT_AUTO, Kf, use_graph, stream, torch)
+            clock[0] += Kf
+            ms_flip[name] = msf / Kf
+        ctx.set_scene_policy(None)
+        if sel_meta is not None:
+            params, norm = selector.load()
+            ctx.load_selector(params, norm)
+        to_cycle_start()
+        base_ms = ms_flip["all_incremental"]
+        flips = {"steps": Kf, "ms_per_step": ms_flip,
+                 "cost_vs_all_incremental": {n: ms / base_ms - 1.0 for n, ms in ms_flip.items() if n != "all_incremental"}}
+
     # ---- the frontier rules (detection only; certificates are exact under each):
     # Algorithm 1's c <= 4 eps_t, the per-point budget c <= 2 (delta_i + eps_t),
     # the cumulative clock 4 (S - S_i) >= c^rev_i
@@ -817,7 +847,7 @@ def main():
                 "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
                 "step_counts": step_counts, "motion": motion, "forward_100": forward, "sustained": sustained,
-                "compare": compare, "regret": regret, "frontier_rules": rules,
+                "compare": compare, "regret": regret, "family_flips": flips, "frontier_rules": rules,
                 "matched_pair": matched_pair, "knn": knn, "single_scene": single, "allpairs": allpairs,
                 "status": cert.STATUS_NAMES[rc] if 0 <= rc < len(cert.STATUS_NAMES) else rc}
         print(json.dumps(line), flush=True)

@@ -320,6 +320,15 @@ cert_status cert_get_features(cert_ctx *ctx, float *h_feat);
  * NULL unloads it.  Synchronises.  Never changes results, only the schedule. */
 cert_status cert_selector_load(cert_ctx *ctx, const float *h_params, const float *h_norm);
 
+/* Per-scene policy (no counterpart in the paper): h_policy[n_scenes] of
+ * CERT_INCREMENTAL / CERT_REBUILD, used by CERT_AUTO in place of
+ * cert_config.policy for scenes without a loaded selector's decision, so that
+ * the strategy of every scene of a batch can be set by hand (for example to
+ * measure what one scene family's choice costs inside the batch).  NULL
+ * clears it.  Synchronises; CERT_EINVAL for other values.  Never changes
+ * results, only the schedule. */
+cert_status cert_set_scene_policy(cert_ctx *ctx, const int32_t *h_policy);
+
 /* Selector training and batch inference on the device (no counterpart in
  * the paper).  X[n][8] raw features, normalised inside the kernels with
  * d_norm[16] (mean[8], 1/std[8]); T[n][2] targets (ln t_inc, ln t_reb);

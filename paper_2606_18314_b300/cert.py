@@ -97,7 +97,7 @@ EXPORTS = ["cert_knn_init", "cert_knn_step", "cert_knn_get_views", "cert_knn_syn
            "cert_allpairs_noalloc", "cert_set_cell_scale", "cert_set_cell_quantile", "cert_get_cell_scale", "cert_autotune",
            "cert_snapshot", "cert_restore", "cert_get_features", "cert_selector_load",
            "cert_mlp_workspace_bytes", "cert_mlp_forward", "cert_mlp_grad", "cert_mlp_adam",
-           "cert_selftest_bounded_wait", "cert_set_step_path", "cert_get_step_path"]
+           "cert_selftest_bounded_wait", "cert_set_step_path", "cert_get_step_path", "cert_set_scene_policy"]
 MLP_PARAMS = 4866
 CERT_FRONTIER_STEP, CERT_FRONTIER_POINT, CERT_FRONTIER_CLOCK = 0, 1, 2
 FRONTIER_RULE = {"step": CERT_FRONTIER_STEP, "point": CERT_FRONTIER_POINT, "clock": CERT_FRONTIER_CLOCK}
@@ -142,6 +142,8 @@ def lib():
     L.cert_restore.argtypes = [vp, vp]
     L.cert_get_features.argtypes = [vp, vp]
     L.cert_selector_load.argtypes = [vp, vp, vp]
+    L.cert_set_scene_policy.argtypes = [vp, vp]
+    L.cert_set_scene_policy.restype = ctypes.c_int
     L.cert_mlp_workspace_bytes.argtypes = [i64]
     L.cert_mlp_workspace_bytes.restype = ctypes.c_size_t
     L.cert_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
@@ -515,6 +517,15 @@ class Context:
         out = np.zeros((self.n_scenes, 8), np.float32)
         _check(lib().cert_get_features(self.h, ctypes.c_void_p(out.ctypes.data)), self.h)
         return out
+
+    def set_scene_policy(self, policy=None):
+        """cert_set_scene_policy: per-scene strategy under "auto" without a selector
+        (a sequence of "incremental"/"rebuild" or CERT_* values; None clears)."""
+        if policy is None:
+            _check(lib().cert_set_scene_policy(self.h, None), self.h)
+            return
+        arr = np.ascontiguousarray([STRATEGY[p] if isinstance(p, str) else int(p) for p in policy], np.int32)
+        _check(lib().cert_set_scene_policy(self.h, ctypes.c_void_p(arr.ctypes.data)), self.h)
 
     def load_selector(self, params, norm):
         """cert_selector_load: params[4866], norm[16] (host float32), or None to unload."""

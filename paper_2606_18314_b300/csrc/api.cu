@@ -58,6 +58,8 @@ struct cert_ctx {
     int32_t *ap_pj = nullptr;
     float *sel_params = nullptr, *sel_norm = nullptr;
     bool have_sel = false;
+    int32_t *scene_policy = nullptr;   // [S] per-scene policy under AUTO without a selector
+    bool have_scene_policy = false;
     float *feat = nullptr;          // [S][8] selector features of the last step
     // snapshot of the mutable state (allocated by the first cert_snapshot)
     char *snap = nullptr;
@@ -217,6 +219,7 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.clk_g = c->clk_g;
     a.cell_scale = c->cell_scale;
     a.cell_quantile = c->cell_quantile;
+    a.scene_policy = c->have_scene_policy ? c->scene_policy : nullptr;
     a.sel_params = c->have_sel ? c->sel_params : nullptr;
     a.sel_norm = c->have_sel ? c->sel_norm : nullptr;
     a.feat = c->feat;
@@ -427,7 +430,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_pd = cv.take<float>(3 * apoff), o_pj = cv.take<int32_t>(3 * apoff),
                  o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16), o_feat = cv.take<float>(S * 8),
                  o_resring = cv.take<cert_scene_result>(2 * S), o_order = cv.take<int32_t>(S),
-                 o_mdil = cv.take<uint32_t>(S * kMotionStride);
+                 o_mdil = cv.take<uint32_t>(S * kMotionStride), o_spol = cv.take<int32_t>(S);
     const int64_t Nclk = (c->frontier_rule == CERT_FRONTIER_CLOCK) ? N : 0;
     const size_t o_clks = cv.take<double>(Nclk), o_clkc = cv.take<float>(Nclk), o_clkg = cv.take<float>(Nclk);
     cv.off = (cv.off + 255) & ~size_t(255);
@@ -478,6 +481,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->ap_pd = (float *)(b + o_pd);
     c->ap_pj = (int32_t *)(b + o_pj);
     c->sel_params = (float *)(b + o_selp);
+    c->scene_policy = (int32_t *)(b + o_spol);
     c->sel_norm = (float *)(b + o_seln);
     c->feat = (float *)(b + o_feat);
     c->order = (int32_t *)(b + o_order);
@@ -900,6 +904,20 @@ cert_status cert_selector_load(cert_ctx *c, const float *h_params, const float *
     CK(c, cudaMemcpy(c->sel_params, h_params, CERT_MLP_PARAMS * sizeof(float), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->sel_norm, h_norm, 16 * sizeof(float), cudaMemcpyHostToDevice));
     c->have_sel = true;
+    ++c->settings_epoch;
+    return CERT_OK;
+}
+
+cert_status cert_set_scene_policy(cert_ctx *c, const int32_t *h_policy)
+{
+    if (!c) return fail(nullptr, CERT_EINVAL, "ctx is NULL");
+    if (h_policy)
+        for (int k = 0; k < c->S; ++k)
+            if (h_policy[k] != STRAT_INC && h_policy[k] != STRAT_REB)
+                return fail(c, CERT_EINVAL, "scene policy must be INCREMENTAL or REBUILD");
+    CK(c, cudaStreamSynchronize(c->last));
+    if (h_policy) CK(c, cudaMemcpy(c->scene_policy, h_policy, size_t(c->S) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    c->have_scene_policy = h_policy != nullptr;
     ++c->settings_epoch;
     return CERT_OK;
 }

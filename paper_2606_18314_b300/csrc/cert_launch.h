@@ -60,6 +60,7 @@ struct StepArgs {
     int strategy, policy;
     float cell_scale;
     float cell_quantile;
+    const int32_t *scene_policy;   // [n_scenes] strategy of each scene under AUTO without a selector (NULL: policy)
     const float *sel_params;       // selector weights (NULL: none loaded)
     const float *sel_norm;         // feature mean[8], 1/std[8] (NULL: none loaded)
     float *feat;                   // [n_scenes][8] selector features of the last step

@@ -174,7 +174,7 @@ __device__ int select_scene(const StepArgs &a, int s, float eps, int nF, double 
     int strat = STRAT_INC;
     if (a.mode == MODE_STEP) {
         strat = a.strategy;
-        if (strat == STRAT_AUTO) strat = a.policy;
+        if (strat == STRAT_AUTO) strat = a.scene_policy ? a.scene_policy[s] : a.policy;
         // ---- the eight selector features of this step (stored every step)
         if (threadIdx.x == 0) {
             const SceneState st = a.st[s];

@@ -250,3 +250,33 @@ def test_shipped_selector_on_held_out_real_transitions(torch):
     assert learned <= always_inc + 0.01
     assert learned < 0.5 * threshold
     assert learned < 0.5 * always_reb
+
+
+def test_scene_policy_sets_each_scenes_strategy_and_keeps_results_exact(torch):
+    """cert_set_scene_policy: under AUTO without a selector every scene takes
+    its own strategy; the certificates stay equal to the oracle's; other values
+    are rejected; clearing it returns to the context policy."""
+    from paper_2606_18314_b300 import cert
+    m = scenes.BatchMotion.mixed(n_scenes=6, lo=300, hi=3000, eps=1e-3, seed=61)
+    off, frames = m.offsets, m.frames(4)
+    ctx = cert.Context(dev(torch, frames[0]), offsets=off, path="multi")
+    refs = [oracle.top2(frames[0][off[s]:off[s + 1]]) for s in range(6)]
+    pol = ["rebuild", "incremental", "incremental", "rebuild", "incremental", "rebuild"]
+    ctx.set_scene_policy(pol)
+    for t in (1, 2, 3):
+        if t == 3:
+            ctx.set_scene_policy(None)
+        ctx.step(dev(torch, frames[t]), 1e-3, "auto")
+        res, rc = ctx.sync()
+        assert rc == cert.CERT_OK
+        nn = ctx.views()["nn"].cpu().numpy()
+        for s in range(6):
+            want = cert.CERT_INCREMENTAL if t == 3 else cert.STRATEGY[pol[s]]
+            assert int(res[s]["strategy"]) == want, (t, s)
+            r = oracle.step(frames[t - 1][off[s]:off[s + 1]], frames[t][off[s]:off[s + 1]], refs[s])
+            assert np.array_equal(nn[off[s]:off[s + 1]], r.cert.nn) and int(res[s]["n_failed"]) == r.n_failed
+            refs[s] = r.cert
+    with pytest.raises(cert.CertError) as ei:
+        ctx.set_scene_policy([cert.CERT_ALLPAIRS] * 6)
+    assert ei.value.code == cert.CERT_EINVAL
+    ctx.close()
