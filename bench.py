@@ -460,6 +460,8 @@ def main():
     ap.add_argument("--knn-steps", type=int, default=240,
                     help="graph-replayed steps per k-nearest-neighbour case (0: skip)")
     ap.add_argument("--compare-steps", type=int, default=256)
+    ap.add_argument("--scene-regret-steps", type=int, default=24,
+                    help="steps of the per-scene cost attribution and regret (0: skip)")
     ap.add_argument("--flip-steps", type=int, default=64,
                     help="steps per variant of the per-family strategy flips inside the batch (0: skip)")
     ap.add_argument("--single-steps", type=int, default=256,
@@ -672,6 +674,55 @@ def main():
         flips = {"steps": Kf, "ms_per_step": ms_flip,
                  "cost_vs_all_incremental": {n: ms / base_ms - 1.0 for n, ms in ms_flip.items() if n != "all_incremental"}}
 
+    # ---- per-scene cost attribution inside the batch (the cost audit) and the regret
+    # against the per-scene, per-step best strategy: each step is run incremental and
+    # rebuild from identical state; a scene's time in a run is its share of the search
+    # and refresh kernels' time (its share of their summed cycles) plus its share of the
+    # other phases by point count
+    scene_regret = None
+    if args.scene_regret_steps > 0 and args.workload == "batched" and args.family is None:
+        cc = cert.Context(dev_frames[0], offsets=offsets, cell_scale=ctx.cell_scale(), audit=("cost",))
+        sizes = np.diff(offsets).astype(np.float64)
+        for k in range(1, 9):
+            cc.step(dev_frames[k], eps, cert.CERT_INCREMENTAL)
+        iph = {n: cert.PHASE_NAMES.index(n) for n in ("search", "scatter_refresh")}
+        att = {"incremental": [], "rebuild": [], "incremental_again": []}
+        for t in range(args.scene_regret_steps):
+            frame = dev_frames[min(9 + t, F)]
+            cc.snapshot()
+            # the state continues incremental; the repeated incremental run measures the noise floor
+            for j, name in enumerate(("rebuild", "incremental_again", "incremental")):
+                if j:
+                    cc.restore()
+                cc.profile_begin(1)
+                cc.step(frame, eps, cert.STRATEGY[name.replace("_again", "")])
+                ph = cc.profile_end()[0].astype(np.float64)
+                r, _ = cc.sync(raise_on_status=False)
+                cyc_s = r["search_cycles"].astype(np.float64)
+                cyc_r = r["refresh_cycles"].astype(np.float64)
+                other = ph.sum() - ph[iph["search"]] - ph[iph["scatter_refresh"]]
+                att[name].append(other * sizes / sizes.sum() + ph[iph["search"]] * cyc_s / max(cyc_s.sum(), 1.0) +
+                                 ph[iph["scatter_refresh"]] * cyc_r / max(cyc_r.sum(), 1.0))
+        cc.close()
+        Ti, Tr, Ti2 = np.array(att["incremental"]), np.array(att["rebuild"]), np.array(att["incremental_again"])
+        best = np.minimum(Ti, Tr)
+        fam_of = np.arange(S) % len(scenes.FAMILIES)
+        scene_regret = {
+            "steps": args.scene_regret_steps,
+            "regret_vs_per_scene_best": {"incremental": float((Ti - best).sum() / best.sum()),
+                                         "rebuild": float((Tr - best).sum() / best.sum())},
+            "rebuild_best_frac": float((Tr < Ti).mean()),
+            "rebuild_best_frac_by_family": {scenes.FAMILIES[f]: float((Tr < Ti)[:, fam_of == f].mean())
+                                            for f in range(len(scenes.FAMILIES))},
+            "gain_of_per_scene_best_over_incremental": float((Ti - best).sum() / Ti.sum()),
+            # the same statistic between two incremental runs of the same steps: what noise in the
+            # per-scene attribution alone makes the per-scene minimum look like
+            "noise_floor_gain": float((Ti - np.minimum(Ti, Ti2)).sum() / Ti.sum()),
+            "noise_floor_flip_frac": float((Ti2 < Ti).mean()),
+            "attribution": "per scene: search and refresh kernel time split by the scene's summed cycles "
+                           "(CERT_AUDIT_COST), the other phases by point count; both strategies from "
+                           "identical state each step"}
+
     # ---- the frontier rules (detection only; certificates are exact under each):
     # Algorithm 1's c <= 4 eps_t, the per-point budget c <= 2 (delta_i + eps_t),
     # the cumulative clock 4 (S - S_i) >= c^rev_i
@@ -847,7 +898,8 @@ def main():
                 "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * K, "clocks": clocks,
                 "step_counts": step_counts, "motion": motion, "forward_100": forward, "sustained": sustained,
-                "compare": compare, "regret": regret, "family_flips": flips, "frontier_rules": rules,
+                "compare": compare, "regret": regret, "family_flips": flips, "scene_regret": scene_regret,
+                "frontier_rules": rules,
                 "matched_pair": matched_pair, "knn": knn, "single_scene": single, "allpairs": allpairs,
                 "status": cert.STATUS_NAMES[rc] if 0 <= rc < len(cert.STATUS_NAMES) else rc}
         print(json.dumps(line), flush=True)

@@ -113,7 +113,10 @@ typedef struct {
  *                        gyration and compactness. */
 typedef enum {
     CERT_AUDIT_RHO = 1,
-    CERT_AUDIT_GEOMETRY = 2
+    CERT_AUDIT_GEOMETRY = 2,
+    CERT_AUDIT_COST = 4       /* per-scene cost attribution inside a batched step (no counterpart
+                                 in the paper): search_cycles, refresh_cycles.  Runs the
+                                 multi-kernel step (the fused step is not taken) */
 } cert_audit;
 
 /* Per-scene scalars of the last step.  Same layout on device and host. */
@@ -150,6 +153,13 @@ typedef struct {
                                  points of the scene), clamped to [0, 1]: 1 when the failures
                                  collapse to a point, near 0 when they spread like the scene;
                                  1 for a single failure, 0 without failures                   */
+    uint64_t search_cycles;   /* CERT_AUDIT_COST: the SM clock cycles the scene's searches took,
+                                 summed over its queries (each query from its set-up to its
+                                 certificate write, on its lane's SM clock, waits for the warp's
+                                 other lanes included).  Within a step the scenes' shares of the
+                                 sum are their shares of the search kernel's time             */
+    uint64_t refresh_cycles;  /* CERT_AUDIT_COST: the same for the scatter and O(1) refresh of
+                                 the scene's points                                             */
 } cert_scene_result;
 
 /* Device views of the per-point results; valid until the next call that

@@ -44,7 +44,8 @@ class cert_scene_result(ctypes.Structure):
                 ("strategy", ctypes.c_int32), ("pred_inc", ctypes.c_float), ("pred_reb", ctypes.c_float),
                 ("grid_res", ctypes.c_int32), ("search_res", ctypes.c_int32),
                 ("n_rho", ctypes.c_int32), ("n_rho_hit", ctypes.c_int32), ("gyration", ctypes.c_double),
-                ("compactness", ctypes.c_double)]
+                ("compactness", ctypes.c_double), ("search_cycles", ctypes.c_uint64),
+                ("refresh_cycles", ctypes.c_uint64)]
 
 
 SCENE_DTYPE = np.dtype([(n, np.dtype(t).newbyteorder("=")) for n, t in [
@@ -54,7 +55,8 @@ SCENE_DTYPE = np.dtype([(n, np.dtype(t).newbyteorder("=")) for n, t in [
     ("failed_cells", np.int32), ("frontier_cells", np.int32), ("occupied_cells", np.int32),
     ("strategy", np.int32), ("pred_inc", np.float32), ("pred_reb", np.float32),
     ("grid_res", np.int32), ("search_res", np.int32), ("n_rho", np.int32), ("n_rho_hit", np.int32),
-    ("gyration", np.float64), ("compactness", np.float64)]])
+    ("gyration", np.float64), ("compactness", np.float64), ("search_cycles", np.uint64),
+    ("refresh_cycles", np.uint64)]])
 assert SCENE_DTYPE.itemsize == ctypes.sizeof(cert_scene_result)
 
 
@@ -320,11 +322,11 @@ def cert_mlp_adam(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e
                                float(beta2), float(eps), _stream_ptr(stream)))
 
 
-AUDIT = {"rho": 1, "geometry": 2}    # cert_audit
+AUDIT = {"rho": 1, "geometry": 2, "cost": 4}    # cert_audit
 
 
 def audit_flags(audit) -> int:
-    """cert_audit flags from an int or names ("rho", "geometry")."""
+    """cert_audit flags from an int or names ("rho", "geometry", "cost")."""
     if isinstance(audit, (int, np.integer)):
         return int(audit)
     if isinstance(audit, str):

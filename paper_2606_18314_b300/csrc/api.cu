@@ -249,6 +249,7 @@ static bool fused_resident(const cert_ctx *c)
 static bool use_fused(const cert_ctx *c, int strategy)
 {
     if (!c->fused_ok || strategy == STRAT_ALL || c->step_path == CERT_PATH_MULTI) return false;
+    if (c->audit & CERT_AUDIT_COST) return false;   // the cost audit instruments the multi-kernel step
     if (c->step_path == CERT_PATH_FUSED) return true;
     return fused_resident(c) && (c->S >= kFusedAutoScenes || c->max_n <= kFusedAutoSingleN);
 }
@@ -329,7 +330,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     if (!d_pos) return fail(nullptr, CERT_EINVAL, "positions are NULL");
     if (cfg->dim != 2 && cfg->dim != 3) return fail(nullptr, CERT_EINVAL, "dim must be 2 or 3");
     if (cfg->n_scenes < 1) return fail(nullptr, CERT_EINVAL, "n_scenes must be >= 1");
-    if (cfg->audit & ~(CERT_AUDIT_RHO | CERT_AUDIT_GEOMETRY)) return fail(nullptr, CERT_EINVAL, "unknown audit flag");
+    if (cfg->audit & ~(CERT_AUDIT_RHO | CERT_AUDIT_GEOMETRY | CERT_AUDIT_COST))
+        return fail(nullptr, CERT_EINVAL, "unknown audit flag");
     if (cfg->frontier_rule < CERT_FRONTIER_STEP || cfg->frontier_rule > CERT_FRONTIER_CLOCK)
         return fail(nullptr, CERT_EINVAL, "unknown frontier_rule");
     if (cfg->bucket_factor != 0 && cfg->bucket_factor != 1 && cfg->bucket_factor != 2 && cfg->bucket_factor != 4 &&

@@ -102,6 +102,8 @@ struct SceneAcc {
     double s_front;                // sum over cells of n ln n, detected frontier
     double f_sum[4];               // geometry audit: sums of x, y, z, |p|^2 over the failures
     double a_sum[4];               // ... and over every point of the scene
+    unsigned long long search_cyc; // cost audit: summed per-query search cycles
+    unsigned long long refresh_cyc;// ... and per-point scatter + refresh cycles
 };
 
 struct Top3 {

@@ -395,6 +395,8 @@ __device__ __forceinline__ void finalize_scene(const StepArgs &a, int s, const S
         r.n_rho_hit = acc.n_rho_hit;
         r.gyration = 0.0;
         r.compactness = 0.0;
+        r.search_cycles = acc.search_cyc;
+        r.refresh_cycles = acc.refresh_cyc;
         if ((a.audit & CERT_AUDIT_GEOMETRY) && acc.n_failed > 0) {
             r.gyration = gyration_radius(acc.f_sum, acc.n_failed);
             const double all = gyration_radius(acc.a_sum, sp.n);

@@ -496,6 +496,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fused_step(const StepArgs a, 
         acc.n_rho = (a.audit & CERT_AUDIT_RHO) ? m.n_rho : 0;
         acc.n_rho_hit = (a.audit & CERT_AUDIT_RHO) ? m.n_rho_hit : 0;
         acc.pad = 0;
+        acc.search_cyc = acc.refresh_cyc = 0ull;   // the cost audit runs the multi-kernel step
         acc.s_fail = fix_to_double(m.s_fail);
         acc.s_front = fix_to_double(m.s_front);
         for (int k = 0; k < 4; ++k) {

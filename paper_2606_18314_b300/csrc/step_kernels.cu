@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
 constexpr int kScatPer = 2;
 constexpr int kSmallGridScatter = 6 * 148;   // one wave of k_scatter_refresh (42 registers)
 
-template <int DIM, int PER>
+template <int DIM, int PER, bool COST>
 __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
 {
     const int base = blockIdx.x * (kThreads * PER) + threadIdx.x;
@@ -387,12 +387,15 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
     }
     int changed[PER], missed[PER], first[PER], hit[PER];
     double dl[PER];
+    double cyc[PER];   // cost audit: this point's scatter + refresh cycles
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int i = base + k * kThreads;
         changed[k] = missed[k] = first[k] = hit[k] = 0;
         dl[k] = 0.0;
+        cyc[k] = 0.0;
         if (s[k] < 0) continue;
+        const long long t0 = COST ? clock64() : 0;
         const SceneParams sp = a.sp[s[k]];
         int slot = a.bucket_start[br[k].x] + br[k].y;
         if ((unsigned)(slot - sp.pt_off) >= (unsigned)sp.n) {  // only after a timed-out scan
@@ -415,8 +418,17 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
             }
         }
         a.sflag[slot] = need ? 1 : 0;
+        if (COST) cyc[k] = (double)(clock64() - t0);
     }
     if (!step) return;  // uniform across the grid
+    if (COST) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const unsigned m = scene_run_mask(s[k]);
+            const double c = run_sum_f64(m, cyc[k]);
+            if (s[k] >= 0 && run_leader(m) && c > 0.0) atomicAdd(&a.acc[s[k]].refresh_cyc, (unsigned long long)c);
+        }
+    }
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const unsigned m = scene_run_mask(s[k]);
@@ -450,7 +462,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
 // lanes per query: the GPU has lanes to spare there, and each lane walks a
 // quarter of its query's quads, which cuts the chain of dependent loads that
 // bounds a lone query's latency.
-template <int DIM, int CHUNK, int G>
+template <int DIM, int CHUNK, int G, bool COST>
 __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 64 registers: 4 CTAs per SM
 {
     constexpr int NR = (DIM == 3) ? 9 : 3;
@@ -483,6 +495,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
         const bool active = e < (int)count;   // the same for the G lanes of a group
         int s = -1;
         SearchOut o = {0, 0, 0, 0, 0.0};
+        const long long t0 = COST ? clock64() : 0;   // cost audit: this query's cycles
         if (active) {
             const int slot = s_list[e];
             s = a.scene_of[slot];        // slot ranges of scenes equal their point ranges
@@ -535,6 +548,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
             const int fc = run_sum_i32(m, o.first);
             const int nh = run_sum_i32(m, o.hit);
             const double sd = run_sum_f64(m, o.dl);
+            if (COST) {
+                const double c = run_sum_f64(m, (active && gl == 0) ? (double)(clock64() - t0) : 0.0);
+                if (s >= 0 && run_leader(m) && c > 0.0) atomicAdd(&a.acc[s].search_cyc, (unsigned long long)c);
+            }
             if (s >= 0 && run_leader(m)) {
                 atomicAdd(&a.acc[s].n_searched, nsr);
                 if (nc) {
@@ -678,6 +695,30 @@ __global__ void k_distances(const float *d1sq, const float *d2sq, float *d1, flo
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
+template <int DIM, bool COST>
+static void launch_scatter(const StepArgs &a, cudaStream_t st)
+{
+    if (nblk(a.n_total, kThreads) <= kSmallGridScatter)
+        k_scatter_refresh<DIM, 1, COST><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(a);
+    else
+        k_scatter_refresh<DIM, kScatPer, COST><<<nblk(a.n_total, kThreads * kScatPer), kThreads, 0, st>>>(a);
+}
+
+template <int DIM, bool COST>
+static void launch_search(const StepArgs &a, cudaStream_t st)
+{
+    if (nblk(a.n_total, kThreads / 8) <= kSearchSmallGrid)
+        k_search<DIM, kThreads / 8, 8, COST><<<nblk(a.n_total, kThreads / 8), kThreads, 0, st>>>(a);
+    else if (nblk(a.n_total, kThreads / 4) <= kSearchSmallGrid)
+        k_search<DIM, kThreads / 4, 4, COST><<<nblk(a.n_total, kThreads / 4), kThreads, 0, st>>>(a);
+    else if (nblk(a.n_total, kSearchChunk / 4) <= kSearchSmallGrid)
+        k_search<DIM, kSearchChunk / 4, 1, COST><<<nblk(a.n_total, kSearchChunk / 4), kThreads, 0, st>>>(a);
+    else if (nblk(a.n_total, kSearchChunk / 2) <= kSearchSmallGrid)
+        k_search<DIM, kSearchChunk / 2, 1, COST><<<nblk(a.n_total, kSearchChunk / 2), kThreads, 0, st>>>(a);
+    else
+        k_search<DIM, kSearchChunk, 1, COST><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
+}
+
 template <int DIM>
 static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
 {
@@ -699,22 +740,16 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
         break;
     case PH_SELECT: k_select<DIM><<<a.n_scenes, kThreads, 0, st>>>(a); break;
     case PH_SCATTER:
-        if (nblk(a.n_total, kThreads) <= kSmallGridScatter)
-            k_scatter_refresh<DIM, 1><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(a);
+        if (a.audit & CERT_AUDIT_COST)
+            launch_scatter<DIM, true>(a, st);
         else
-            k_scatter_refresh<DIM, kScatPer><<<nblk(a.n_total, kThreads * kScatPer), kThreads, 0, st>>>(a);
+            launch_scatter<DIM, false>(a, st);
         break;
     case PH_SEARCH:
-        if (nblk(a.n_total, kThreads / 8) <= kSearchSmallGrid)
-            k_search<DIM, kThreads / 8, 8><<<nblk(a.n_total, kThreads / 8), kThreads, 0, st>>>(a);
-        else if (nblk(a.n_total, kThreads / 4) <= kSearchSmallGrid)
-            k_search<DIM, kThreads / 4, 4><<<nblk(a.n_total, kThreads / 4), kThreads, 0, st>>>(a);
-        else if (nblk(a.n_total, kSearchChunk / 4) <= kSearchSmallGrid)
-            k_search<DIM, kSearchChunk / 4, 1><<<nblk(a.n_total, kSearchChunk / 4), kThreads, 0, st>>>(a);
-        else if (nblk(a.n_total, kSearchChunk / 2) <= kSearchSmallGrid)
-            k_search<DIM, kSearchChunk / 2, 1><<<nblk(a.n_total, kSearchChunk / 2), kThreads, 0, st>>>(a);
+        if (a.audit & CERT_AUDIT_COST)
+            launch_search<DIM, true>(a, st);
         else
-            k_search<DIM, kSearchChunk, 1><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
+            launch_search<DIM, false>(a, st);
         // far queries are rare: a small grid gets a few CTAs (each scans a whole scene per query)
         if (cudaPeekAtLastError() == cudaSuccess)
             k_far<DIM><<<std::min(kFarCtas, std::max(8, nblk(a.n_total, 4096))), kThreads, 0, st>>>(a);

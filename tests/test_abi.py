@@ -66,7 +66,7 @@ def test_host_argument_validation_without_gpu(L):
     cfg.n_total = 2
     assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
     cfg.n_total = 10
-    cfg.audit = 4
+    cfg.audit = 8   # rho = 1, geometry = 2, cost = 4; other bits are rejected
     assert L.cert_init(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(16), None) == cert.CERT_EINVAL
     assert b"audit" in L.cert_last_error(None)
     cfg.audit = 0
@@ -91,8 +91,8 @@ def test_host_argument_validation_without_gpu(L):
 
 def test_struct_layouts_match_header():
     from paper_2606_18314_b300 import cert
-    # cert_scene_result: 2 doubles + 18 four-byte fields + 2 doubles
-    assert ctypes.sizeof(cert.cert_scene_result) == 16 + 18 * 4 + 16
+    # cert_scene_result: 2 doubles + 18 four-byte fields + 2 doubles + 2 uint64 cycle counts
+    assert ctypes.sizeof(cert.cert_scene_result) == 16 + 18 * 4 + 16 + 16
     assert ctypes.sizeof(cert.cert_config) == 4 + 4 + 8 + 8 + 4 + 4 + 16
 
 

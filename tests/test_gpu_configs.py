@@ -125,3 +125,31 @@ def test_localized_motion_16000_d3_200_steps_checked_every_step(torch, family):
         searched.append(int(res[0]["n_searched"]))
     ctx.close()
     print(family, "searched fraction over the last 100 steps", np.mean(searched[100:]) / n)
+
+
+def test_localized_motion_d2_100_steps_checked_every_step(torch):
+    """The refresh's local motion bound at d = 2 (a 16 x 16 motion grid): a
+    hotspot scene of 4,000 points, eps = 1e-3, 100 incremental steps with the
+    two step paths alternating, every step against the oracle; once eps_t has
+    eaten the static points' margins, they are proven by the local bound and
+    the searched fraction falls far below the detected frontier."""
+    from paper_2606_18314_b300 import cert
+    steps, n, eps = 100, 4000, 1e-3
+    m = scenes.Motion("hotspot", n, 2, eps, seed=23, steps=steps)
+    frames = m.frames(steps)
+    dev = torch.from_numpy(frames).cuda()
+    ctx = cert.Context(dev[0])
+    ref = oracle.top2(frames[0])
+    searched, detected = [], []
+    for t in range(1, steps + 1):
+        ctx.set_step_path("fused" if t % 2 else "multi")
+        ctx.step(dev[t], eps, "incremental")
+        res, rc = ctx.sync()
+        assert rc == cert.CERT_OK
+        r = oracle.step(frames[t - 1], frames[t], ref)
+        assert_step_equal(ctx, res, ctx.views(), r, tag=f"d2 hotspot step {t}")
+        ref = r.cert
+        searched.append(int(res[0]["n_searched"]))
+        detected.append(int(res[0]["n_frontier"]))
+    ctx.close()
+    assert np.mean(searched[50:]) < 0.25 * np.mean(detected[50:]), (np.mean(searched[50:]), np.mean(detected[50:]))

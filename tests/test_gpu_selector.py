@@ -280,3 +280,35 @@ def test_scene_policy_sets_each_scenes_strategy_and_keeps_results_exact(torch):
         ctx.set_scene_policy([cert.CERT_ALLPAIRS] * 6)
     assert ei.value.code == cert.CERT_EINVAL
     ctx.close()
+
+
+def test_cost_audit_attributes_cycles_and_keeps_results_exact(torch):
+    """CERT_AUDIT_COST: the multi-kernel step (even when the fused one is asked
+    for) records per scene the summed search and refresh cycles; results stay
+    equal to the oracle's and to an unaudited context's; a scene without
+    searches has no search cycles."""
+    from paper_2606_18314_b300 import cert
+    m = scenes.BatchMotion.mixed(n_scenes=5, lo=400, hi=3000, eps=1e-3, seed=71)
+    off, frames = m.offsets, m.frames(4)
+    ca = cert.Context(dev(torch, frames[0]), offsets=off, audit=("cost",), path="fused")
+    cb = cert.Context(dev(torch, frames[0]), offsets=off)
+    assert ca.step_path("incremental") == "multi"
+    refs = [oracle.top2(frames[0][off[s]:off[s + 1]]) for s in range(5)]
+    for t, strat in ((1, "incremental"), (2, "rebuild"), (3, "incremental")):
+        for c in (ca, cb):
+            c.step(dev(torch, frames[t]), 1e-3, strat)
+        ra, rca = ca.sync()
+        rb, _ = cb.sync()
+        assert rca == cert.CERT_OK
+        assert torch.equal(ca.views()["nn"], cb.views()["nn"])
+        assert torch.equal(ca.views()["d2sq"].view(torch.int32), cb.views()["d2sq"].view(torch.int32))
+        nn = ca.views()["nn"].cpu().numpy()
+        for s in range(5):
+            r = oracle.step(frames[t - 1][off[s]:off[s + 1]], frames[t][off[s]:off[s + 1]], refs[s])
+            assert np.array_equal(nn[off[s]:off[s + 1]], r.cert.nn) and int(ra[s]["n_failed"]) == r.n_failed
+            refs[s] = r.cert
+            assert (int(ra[s]["search_cycles"]) > 0) == (int(ra[s]["n_searched"]) > 0), (t, s)
+            assert int(ra[s]["refresh_cycles"]) > 0, (t, s)
+            assert int(rb[s]["search_cycles"]) == 0 and int(rb[s]["refresh_cycles"]) == 0
+    ca.close()
+    cb.close()
