@@ -1,36 +1,44 @@
 // step_kernels.cu -- the per-step kernels of the certificate-maintenance loop.
 //
 // One step (Algorithm 1 of the paper, every certificate exact afterwards as in
-// Cor. A.2) runs as five kernels over all scenes of a batch at once:
+// Cor. A.2) runs as seven kernels over all scenes of a batch at once, after a
+// clear of the per-step counters:
 //
 //   k_prepare          pack p' to float4, eps_t max-reduce (Alg. 1 first
 //                      statement), search-grid bucket + rank (counting sort,
-//                      histogram phase), entropy-grid cell + occupancy (Def. 2)
+//                      histogram phase), entropy-grid cell + occupancy (Def. 2),
+//                      the per-scene motion grid (largest step per coarse cell)
 //   k_scan             decoupled look-back scans: bucket starts (counting sort,
 //                      scan phase) and the ascending frontier list
 //                      F = {i : c_i <= 4 eps_t + tau_i} (Alg. 1 second
 //                      statement, Lemma 1) with the frontier-cell histogram
 //   k_select           per scene: truncated medians, next search resolution,
-//                      the strategy (forced, policy or learned selector)
+//                      the strategy (forced, per-scene policy, Prop. 1's
+//                      threshold or the learned selector), the motion grid's
+//                      dilation
 //   k_scatter_refresh  counting-sort scatter into cell order; O(1) refresh of
 //                      every certificate that its extended certificate still
 //                      proves (frontier points included)
-//   k_search           grid repair of the flagged points: top-2 over the 3^d
-//                      block, widened until the runner-up is enclosed (Alg. 1
-//                      block loop; Cor. A.2 widening)
+//   k_search           grid repair of the flagged points: top-2 over a box of
+//                      cells sized from the refresh's hint (else the 3^d block),
+//                      widened until the runner-up is enclosed (Alg. 1 block
+//                      loop; Cor. A.2 widening)
+//   k_far              the queries whose box would grow too far: one CTA scans
+//                      the whole scene
 //   k_finalize         per scene: H(F_t) (Def. 2), audit counts, next grid
 //
 // Extended certificate (an addition to the paper's record, needed because the
 // paper leaves d1, d2 of safe points stale while every certificate here is
 // exact each step): besides (nn, d1^2, d2^2) each point keeps its runner-up
-// index nn2 and a lower bound L on the distance to every point other than nn
-// and nn2.  A step changes the distance from i to any j by at most
-// |p'_i - p_i| + eps_t (triangle inequality, as in Lemma 1), so L minus that
-// bounds the next step; when both fresh distances to nn and nn2 stay below it
-// the top-2 is exactly {nn, nn2} in fresh order, otherwise the point is
-// repaired by a search.  The test is independent of the safety rule, so a
-// frontier point it proves is repaired in O(1) too (a change of nn is then
-// found by the reordering of {nn, nn2}).
+// index nn2, a third candidate nn3 and a lower bound L on the distance to
+// every point other than the three.  A step changes the distance from i to
+// any j by at most |p'_i - p_i| + |p'_j - p_j| (triangle inequality, as in
+// Lemma 1), so L minus a bound on that bounds the next step (refresh_point,
+// cert_phases.cuh: eps_t, else the local motion grid); when the second of the
+// three fresh keys stays below it, the first two keys are the exact top-2,
+// otherwise the point is repaired by a search.  The test is independent of the
+// safety rule, so a frontier point it proves is repaired in O(1) too (a change
+// of nn is then found by the reordering of the candidates).
 #include <algorithm>
 
 #include "cert_phases.cuh"
