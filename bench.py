@@ -82,7 +82,7 @@ def phase_bytes(ph, N, dim, n_buckets, n_front, n_searched, zero_bytes, n_tried=
 # on.  The bench line carries the figure only while the loaded library
 # reports the same fingerprint and the run uses one of these cell scales;
 # otherwise it reports null until the capture is taken again.
-SEARCH_TRAFFIC = {"fingerprint": "333b31ba173e96f0", "commit": "the commit after b091c95",
+SEARCH_TRAFFIC = {"fingerprint": "333b31ba173e96f0", "commit": "9dc4abc",
                   "bytes": {3.5: 145.17e6, 4.0: 144.04e6}}
 
 
