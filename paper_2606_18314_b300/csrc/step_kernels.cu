@@ -481,7 +481,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ int s_list[CHUNK];
     __shared__ int2 s_rng[(kMaxRows > NR ? kMaxRows : NR) * NQ];   // per-query row ranges, column-major
+    __shared__ int s_next;                                          // G == 1: the next unclaimed batch
     const int base = blockIdx.x * CHUNK + threadIdx.x * PER;
+    if (threadIdx.x == 0) s_next = kThreads;   // every warp's first batch of 32 is its own
     // flags beyond n_total are zero up to the padded length (a multiple of the
     // scan tile, itself a multiple of CHUNK); each flag byte is 0 or 1
     uint32_t fw = 0u;
@@ -496,10 +498,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
         if ((fw >> (8 * u)) & 0xffu) s_list[pre++] = base + u;
     __syncthreads();
 
+    // G == 1: a warp searches a batch of 32 consecutive queries, then claims the
+    // CTA's next unclaimed batch, so warps that drew short boxes take more
+    // batches instead of idling while one warp finishes its last.  G > 1 (small
+    // grids, one round): NQ queries per round, G lanes each.
     const int gl = (G > 1) ? (int)(threadIdx.x % G) : 0;   // lane within the query's group
-    for (int r0 = 0; r0 < (int)count; r0 += NQ) {
-        if (r0 + (int)(threadIdx.x & ~31u) / G >= (int)count) break;  // whole idle warps leave together
-        const int e = r0 + (int)threadIdx.x / G;
+    const int lane = (int)(threadIdx.x & 31u);
+    for (int r0 = (G == 1) ? (int)(threadIdx.x & ~31u) : 0;;) {
+        if (r0 >= (int)count) break;
+        if (G > 1 && r0 + (int)(threadIdx.x & ~31u) / G >= (int)count) break;  // whole idle warps leave together
+        const int e = (G == 1) ? r0 + lane : r0 + (int)threadIdx.x / G;
         const bool active = e < (int)count;   // the same for the G lanes of a group
         int s = -1;
         SearchOut o = {0, 0, 0, 0, 0.0};
@@ -570,6 +578,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
                     atomicAdd(&a.acc[s].s_fail, sd);
                 }
             }
+        }
+        if (G == 1) {   // the warp's next batch
+            int nb = 0;
+            if (lane == 0) nb = atomicAdd(&s_next, 32);
+            r0 = __shfl_sync(kFull, nb, 0);
+        } else {
+            r0 += NQ;
         }
     }
 }
