@@ -99,6 +99,7 @@ struct cert_ctx {
     uint64_t *tstat_b = nullptr, *tstat_p = nullptr;
     int32_t *bucket_count = nullptr, *hocc = nullptr, *hfail = nullptr, *hcand = nullptr;
     uint32_t *mgrid = nullptr, *mdil = nullptr;   // motion grid (zeroed every step) and its dilation
+    int32_t *chunk_cnt = nullptr, *chunk_order = nullptr;   // batch search: chunk weights and dispatch order
     cudaStream_t last = nullptr;
     bool stepped = false;
     // phase profiling (diagnostics)
@@ -183,6 +184,8 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.status = c->status;
     a.bucket_count = c->bucket_count;
     a.mgrid = c->mgrid;
+    a.chunk_cnt = c->chunk_cnt;
+    a.chunk_order = c->chunk_order;
     a.mdil = c->mdil;
     a.bucket_start = c->bucket_start;
     a.brank = c->brank;
@@ -432,7 +435,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
                  o_pd = cv.take<float>(3 * apoff), o_pj = cv.take<int32_t>(3 * apoff),
                  o_selp = cv.take<float>(8192), o_seln = cv.take<float>(16), o_feat = cv.take<float>(S * 8),
                  o_resring = cv.take<cert_scene_result>(2 * S), o_order = cv.take<int32_t>(S),
-                 o_mdil = cv.take<uint32_t>(S * kMotionStride), o_spol = cv.take<int32_t>(S);
+                 o_mdil = cv.take<uint32_t>(S * kMotionStride), o_spol = cv.take<int32_t>(S),
+                 o_ccnt = cv.take<int32_t>(ceil_div(N, kSearchChunk)), o_cord = cv.take<int32_t>(ceil_div(N, kSearchChunk));
     const int64_t Nclk = (c->frontier_rule == CERT_FRONTIER_CLOCK) ? N : 0;
     const size_t o_clks = cv.take<double>(Nclk), o_clkc = cv.take<float>(Nclk), o_clkg = cv.take<float>(Nclk);
     cv.off = (cv.off + 255) & ~size_t(255);
@@ -488,6 +492,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->feat = (float *)(b + o_feat);
     c->order = (int32_t *)(b + o_order);
     c->mdil = (uint32_t *)(b + o_mdil);
+    c->chunk_cnt = (int32_t *)(b + o_ccnt);
+    c->chunk_order = (int32_t *)(b + o_cord);
     c->mgrid = (uint32_t *)(b + o_mgrid);
     if (Nclk) {
         c->clk_s = (double *)(b + o_clks);
@@ -554,6 +560,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->status, 0, 4 * sizeof(uint32_t), s);
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->fstart, 0, (S + 1) * sizeof(int32_t), s);
         if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->feat, 0, S * 8 * sizeof(float), s);
+        if (e3 == cudaSuccess) e3 = cudaMemsetAsync(c->chunk_cnt, 0, ceil_div(N, kSearchChunk) * sizeof(int32_t), s);
         if (e3 != cudaSuccess) rc = cuda_fail(c, "cudaMemsetAsync", e3);
     }
     if (rc == CERT_OK) rc = run_full(c, MODE_INIT, d_pos, s);

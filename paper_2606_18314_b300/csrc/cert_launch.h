@@ -38,6 +38,8 @@ struct StepArgs {
     uint32_t *mdil;                // [n_scenes][kMotionStride] its dilation by one cell
     uint8_t *sflag;                // [n_pad] by sorted slot: 1 = search this point
     int32_t *far_list;             // [n] sorted slots left to the far pass
+    int32_t *chunk_cnt;            // [n_chunks] queries each batch search chunk had (kept for the next step)
+    int32_t *chunk_order;          // [n_chunks] the search's CTA -> chunk map, heaviest chunks first
     int32_t *far_count;            // number of entries in far_list (zeroed every call)
     // certificates
     int frontier_rule;             // cert_frontier_rule

@@ -482,7 +482,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
     __shared__ int s_list[CHUNK];
     __shared__ int2 s_rng[(kMaxRows > NR ? kMaxRows : NR) * NQ];   // per-query row ranges, column-major
     __shared__ int s_next;                                          // G == 1: the next unclaimed batch
-    const int base = blockIdx.x * CHUNK + threadIdx.x * PER;
+    // the batch's CTAs take their chunks heaviest first (k_chunk_order, from the
+    // query counts the chunks had in the previous step)
+    constexpr bool kOrdered = (CHUNK == kSearchChunk && G == 1);
+    const int chunk = kOrdered ? a.chunk_order[blockIdx.x] : (int)blockIdx.x;
+    const int base = chunk * CHUNK + threadIdx.x * PER;
     if (threadIdx.x == 0) s_next = kThreads;   // every warp's first batch of 32 is its own
     // flags beyond n_total are zero up to the padded length (a multiple of the
     // scan tile, itself a multiple of CHUNK); each flag byte is 0 or 1
@@ -496,6 +500,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
 #pragma unroll
     for (int u = 0; u < PER; ++u)
         if ((fw >> (8 * u)) & 0xffu) s_list[pre++] = base + u;
+    if (kOrdered && threadIdx.x == 0) a.chunk_cnt[chunk] = (int)count;   // the next step's order
     __syncthreads();
 
     // G == 1: a warp searches a batch of 32 consecutive queries, then claims the
@@ -587,6 +592,32 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
             r0 += NQ;
         }
     }
+}
+
+// ============================================================================ k_chunk_order
+
+// The batch search's dispatch order: chunks sorted by the number of queries they
+// had in the previous step, heaviest first (a counting sort on 32 classes of 32
+// queries), so that long CTAs start early and the last ones dispatched are
+// short; the SMs then run out of work together.  The order only schedules:
+// every chunk is searched once whatever it is.
+__global__ void __launch_bounds__(1024) k_chunk_order(const StepArgs a, int nch)
+{
+    __shared__ int s_hist[32], s_start[32];
+    if (threadIdx.x < 32) s_hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < nch; c += 1024) atomicAdd(&s_hist[31 - min(31, a.chunk_cnt[c] >> 5)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < 32; ++b) {
+            s_start[b] = run;
+            run += s_hist[b];
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nch; c += 1024)
+        a.chunk_order[atomicAdd(&s_start[31 - min(31, a.chunk_cnt[c] >> 5)], 1)] = c;
 }
 
 // ============================================================================ k_far
@@ -738,8 +769,10 @@ static void launch_search(const StepArgs &a, cudaStream_t st)
         k_search<DIM, kSearchChunk / 4, 1, COST><<<nblk(a.n_total, kSearchChunk / 4), kThreads, 0, st>>>(a);
     else if (nblk(a.n_total, kSearchChunk / 2) <= kSearchSmallGrid)
         k_search<DIM, kSearchChunk / 2, 1, COST><<<nblk(a.n_total, kSearchChunk / 2), kThreads, 0, st>>>(a);
-    else
+    else {
+        k_chunk_order<<<1, 1024, 0, st>>>(a, nblk(a.n_total, kSearchChunk));
         k_search<DIM, kSearchChunk, 1, COST><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
+    }
 }
 
 template <int DIM>
