@@ -74,6 +74,7 @@ struct KnnCounters {
     int32_t far_count;       // entries of the far list
     int32_t heavy_count;     // entries of the heavy list
     int32_t n_frontier, n_failed, n_missed, n_searched;
+    int32_t search_next;     // the search list's next unclaimed batch of 32 (k_knn_search)
 };
 
 // One level of the hashed grid.
@@ -581,7 +582,18 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn_search(const KnnArgs a)
     const KnnGrid grid = *a.grid;
     const int k = a.k, S = a.S;
     int searched = 0, changed_sum = 0, missed_sum = 0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    // A warp claims the list's next batch of 32 queries (one per lane) when its
+    // previous batch is done: the queries' costs vary widely, and a fixed
+    // grid-stride share would leave the warps that drew cheap ones idle while a
+    // few finish long ones.
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t0 = 0;
+        if (lane == 0) t0 = atomicAdd(&a.ctr->search_next, 32);
+        t0 = __shfl_sync(kFull, t0, 0);
+        if (t0 >= total) break;
+        const int t = t0 + lane;
+        if (t >= total) continue;   // the last batch's idle lanes go straight to the next claim
         const int i = a.need[t];
         const float4 p = a.pos_new[i];
         KnnLevel gr;
