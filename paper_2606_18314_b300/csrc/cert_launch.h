@@ -40,6 +40,7 @@ struct StepArgs {
     int32_t *far_list;             // [n] sorted slots left to the far pass
     int32_t *chunk_cnt;            // [n_chunks] queries each batch search chunk had (kept for the next step)
     int32_t *chunk_order;          // [n_chunks] the search's CTA -> chunk map, heaviest chunks first
+    int order_chunks;              // k_prepare's first CTA orders this many chunks (0: the search is unordered)
     int32_t *far_count;            // number of entries in far_list (zeroed every call)
     // certificates
     int frontier_rule;             // cert_frontier_rule

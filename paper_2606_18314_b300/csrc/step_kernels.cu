@@ -54,9 +54,15 @@ namespace certk {
 constexpr int kPrepPer = 4;
 constexpr int kSmallGridPrepare = 5 * 148;   // one wave of k_prepare (48 registers)
 
+__device__ void order_chunks(const StepArgs &a, int nch, int *s_hist, int *s_start);
+
 template <int DIM, int PER>
 __global__ void __launch_bounds__(kThreads, 5) k_prepare(const StepArgs a)   // 48 registers: 5 CTAs per SM
 {
+    if (a.order_chunks > 0 && blockIdx.x == 0) {   // uniform in the CTA
+        __shared__ int s_hist[32], s_start[32];
+        order_chunks(a, a.order_chunks, s_hist, s_start);
+    }
     const int base = blockIdx.x * (kThreads * PER) + threadIdx.x;
     int s[PER];
     float4 p[PER], po[PER];
@@ -594,19 +600,20 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
     }
 }
 
-// ============================================================================ k_chunk_order
+// ============================================================================ chunk order
 
 // The batch search's dispatch order: chunks sorted by the number of queries they
 // had in the previous step, heaviest first (a counting sort on 32 classes of 32
 // queries), so that long CTAs start early and the last ones dispatched are
 // short; the SMs then run out of work together.  The order only schedules:
-// every chunk is searched once whatever it is.
-__global__ void __launch_bounds__(1024) k_chunk_order(const StepArgs a, int nch)
+// every chunk is searched once whatever it is.  Run by one whole CTA (the first
+// CTA of k_prepare, alongside its points: the counts come from the previous
+// step's k_search, the order is read by this step's).
+__device__ void order_chunks(const StepArgs &a, int nch, int *s_hist, int *s_start)
 {
-    __shared__ int s_hist[32], s_start[32];
     if (threadIdx.x < 32) s_hist[threadIdx.x] = 0;
     __syncthreads();
-    for (int c = threadIdx.x; c < nch; c += 1024) atomicAdd(&s_hist[31 - min(31, a.chunk_cnt[c] >> 5)], 1);
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) atomicAdd(&s_hist[31 - min(31, a.chunk_cnt[c] >> 5)], 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         int run = 0;
@@ -616,7 +623,7 @@ __global__ void __launch_bounds__(1024) k_chunk_order(const StepArgs a, int nch)
         }
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < nch; c += 1024)
+    for (int c = threadIdx.x; c < nch; c += blockDim.x)
         a.chunk_order[atomicAdd(&s_start[31 - min(31, a.chunk_cnt[c] >> 5)], 1)] = c;
 }
 
@@ -769,25 +776,33 @@ static void launch_search(const StepArgs &a, cudaStream_t st)
         k_search<DIM, kSearchChunk / 4, 1, COST><<<nblk(a.n_total, kSearchChunk / 4), kThreads, 0, st>>>(a);
     else if (nblk(a.n_total, kSearchChunk / 2) <= kSearchSmallGrid)
         k_search<DIM, kSearchChunk / 2, 1, COST><<<nblk(a.n_total, kSearchChunk / 2), kThreads, 0, st>>>(a);
-    else {
-        k_chunk_order<<<1, 1024, 0, st>>>(a, nblk(a.n_total, kSearchChunk));
+    else   // chunk_order was written by k_prepare's first CTA (search_ordered)
         k_search<DIM, kSearchChunk, 1, COST><<<nblk(a.n_total, kSearchChunk), kThreads, 0, st>>>(a);
-    }
+}
+
+// Whether the search takes the batch's ordered full chunks (the last branch above).
+static bool search_ordered(long long n)
+{
+    return nblk(n, kThreads / 4) > kSearchSmallGrid && nblk(n, kSearchChunk / 4) > kSearchSmallGrid &&
+           nblk(n, kSearchChunk / 2) > kSearchSmallGrid;
 }
 
 template <int DIM>
 static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
 {
     switch (phase) {
-    case PH_PREPARE:
+    case PH_PREPARE: {
+        StepArgs b = a;
+        b.order_chunks = search_ordered(a.n_total) ? nblk(a.n_total, kSearchChunk) : 0;
         // the fewest points per thread whose grid still fits one wave (5 CTAs per SM)
         if (nblk(a.n_total, kThreads) <= kSmallGridPrepare)
-            k_prepare<DIM, 1><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(a);
+            k_prepare<DIM, 1><<<nblk(a.n_total, kThreads), kThreads, 0, st>>>(b);
         else if (nblk(a.n_total, kThreads * 2) <= kSmallGridPrepare)
-            k_prepare<DIM, 2><<<nblk(a.n_total, kThreads * 2), kThreads, 0, st>>>(a);
+            k_prepare<DIM, 2><<<nblk(a.n_total, kThreads * 2), kThreads, 0, st>>>(b);
         else
-            k_prepare<DIM, kPrepPer><<<nblk(a.n_total, kThreads * kPrepPer), kThreads, 0, st>>>(a);
+            k_prepare<DIM, kPrepPer><<<nblk(a.n_total, kThreads * kPrepPer), kThreads, 0, st>>>(b);
         break;
+    }
     case PH_SCAN:
         if (a.ntiles_b + a.ntiles_p < kScanLatencyTiles)
             k_scan<DIM, true><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a);
