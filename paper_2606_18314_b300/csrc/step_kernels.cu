@@ -205,11 +205,15 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     __shared__ uint32_t s_excl;
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(a.tile_ctr, 1u);
     __syncthreads();
+    // Point tiles take the first tickets: they are the longer ones (the
+    // frontier test and the cell atomics), so they start early and the short
+    // bucket tiles fill in at the end.  Each chain still takes its tiles in order.
     const int t = s_tile;
 
-    if (t < a.ntiles_b) {
+    if (t >= a.ntiles_p) {
         // ---- bucket counts -> bucket starts (global exclusive scan over all scenes)
-        const int base = t * kScanTile + threadIdx.x * kScanItems;
+        const int tb = t - a.ntiles_p;
+        const int base = tb * kScanTile + threadIdx.x * kScanItems;
         uint32_t v[kScanItems];
 #pragma unroll
         for (int k = 0; k < kScanItems; k += 4) {
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
         uint32_t tot;
         const uint32_t pre = block_exclusive_scan(sum, &tot, s_warp);
         if (threadIdx.x < 32) {
-            const uint32_t ex = lookback(a.tstat_b, t, tot, a.status);
+            const uint32_t ex = lookback(a.tstat_b, tb, tot, a.status);
             if (threadIdx.x == 0) s_excl = ex;
         }
         __syncthreads();
@@ -243,7 +247,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     }
 
     // ---- frontier flags -> ascending frontier list (Algorithm 1, Lemma 1)
-    const int tp = t - a.ntiles_b;
+    const int tp = t;
     const int base = tp * kScanTile + threadIdx.x * kScanItems;
     uint32_t f[kScanItems];
     uint32_t rho = 0u;                 // bit k: item k flagged by the rho heuristic
