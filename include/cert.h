@@ -303,8 +303,8 @@ cert_status cert_autotune(cert_ctx *ctx, const float *d_frames, int64_t frame_st
                           float eps, int32_t strategy, const float *h_scales, int32_t n_scales, float *h_ms,
                           float *h_best, void *stream);
 
-/* Copy the mutable state (positions, extended certificates, per-scene state
- * and the last step's outputs) aside / put it back, so that several
+/* Copy the mutable state (positions, extended certificates, per-scene state,
+ * the last step's outputs and the search's schedule) aside / put it back, so that several
  * strategies can be run and timed from identical state.  The first
  * cert_snapshot allocates its buffer (about 46 bytes per point); restore
  * without a snapshot returns CERT_ESTATE.  Stream-ordered. */

@@ -942,7 +942,10 @@ static std::vector<std::pair<void *, size_t>> snapshot_pieces(cert_ctx *c)
             {c->hcell, N * 4},                     {c->frontier, N * 4},   {c->fstart, (S + 1) * 4},
             {c->failed, N},                        {c->inF, N},            {c->feat, S * 8 * 4},
             {c->clk_s, c->clk_s ? N * 8 : 0},      {c->clk_c, c->clk_c ? N * 4 : 0},
-            {c->clk_g, c->clk_g ? N * 4 : 0}};
+            {c->clk_g, c->clk_g ? N * 4 : 0},
+            // the search's per-chunk query counts, which order the next step's search:
+            // runs from one snapshot all start from the same schedule
+            {c->chunk_cnt, size_t(ceil_div(int64_t(N), kSearchChunk)) * 4}};
 }
 
 cert_status cert_snapshot(cert_ctx *c, void *stream)
