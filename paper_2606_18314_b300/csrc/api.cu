@@ -442,7 +442,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     cv.off = (cv.off + 255) & ~size_t(255);
     const size_t zero_begin = cv.off;
     const size_t o_acc = cv.take<SceneAcc>(S), o_ctr = cv.take<uint32_t>(4), o_farc = cv.take<int32_t>(4),
-                 o_tb = cv.take<uint64_t>(c->ntiles_b), o_tp = cv.take<uint64_t>(c->ntiles_p),
+                 o_tb = cv.take<uint64_t>(c->ntiles_b * (kScanItems / 2)),
+                 o_tp = cv.take<uint64_t>(ceil_div(N, kThreads * 2)),   // small grids scan quarter tiles
                  o_bcount = cv.take<int32_t>(c->n_buckets_pad), o_hocc = cv.take<int32_t>(hoff),
                  o_hfail = cv.take<int32_t>(hoff), o_hcand = cv.take<int32_t>(hoff),
                  o_mgrid = cv.take<uint32_t>(S * kMotionStride);

@@ -197,9 +197,11 @@ __device__ uint32_t lookback(uint64_t *tstat, int tile, uint32_t aggregate, uint
 // time): the frontier items' entropy cells are loaded with the flags and their
 // atomics issued back to back.  The default order keeps 48 registers, five
 // resident CTAs per SM, for the many-tile grids that are bound by resident CTAs.
-template <int DIM, bool LAT>
+template <int DIM, bool LAT, int ITEMS>
 __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
 {
+    constexpr int TILE = kThreads * ITEMS;
+    static_assert(ITEMS == 2 || ITEMS % 4 == 0, "bucket counts load two or four at a time");
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ int s_tile;
     __shared__ uint32_t s_excl;
@@ -213,19 +215,25 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     if (t >= a.ntiles_p) {
         // ---- bucket counts -> bucket starts (global exclusive scan over all scenes)
         const int tb = t - a.ntiles_p;
-        const int base = tb * kScanTile + threadIdx.x * kScanItems;
-        uint32_t v[kScanItems];
+        const int base = tb * TILE + threadIdx.x * ITEMS;
+        uint32_t v[ITEMS];
+        if constexpr (ITEMS == 2) {
+            const int2 c2 = *reinterpret_cast<const int2 *>(a.bucket_count + base);
+            v[0] = (uint32_t)c2.x;
+            v[ITEMS > 1 ? 1 : 0] = (uint32_t)c2.y;
+        } else {
 #pragma unroll
-        for (int k = 0; k < kScanItems; k += 4) {
-            const int4 c4 = *reinterpret_cast<const int4 *>(a.bucket_count + base + k);
-            v[k] = (uint32_t)c4.x;
-            v[k + 1] = (uint32_t)c4.y;
-            v[k + 2] = (uint32_t)c4.z;
-            v[k + 3] = (uint32_t)c4.w;
+            for (int k = 0; k < ITEMS; k += 4) {
+                const int4 c4 = *reinterpret_cast<const int4 *>(a.bucket_count + base + k);
+                v[k] = (uint32_t)c4.x;
+                v[k + 1] = (uint32_t)c4.y;
+                v[k + 2] = (uint32_t)c4.z;
+                v[k + 3] = (uint32_t)c4.w;
+            }
         }
         uint32_t sum = 0u;
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) sum += v[k];
+        for (int k = 0; k < ITEMS; ++k) sum += v[k];
         uint32_t tot;
         const uint32_t pre = block_exclusive_scan(sum, &tot, s_warp);
         if (threadIdx.x < 32) {
@@ -234,29 +242,33 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
         }
         __syncthreads();
         uint32_t run = s_excl + pre;
-        int o[kScanItems];
+        int o[ITEMS];
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
+        for (int k = 0; k < ITEMS; ++k) {
             o[k] = (int)run;
             run += v[k];
         }
+        if constexpr (ITEMS == 2) {
+            *reinterpret_cast<int2 *>(a.bucket_start + base) = make_int2(o[0], o[ITEMS > 1 ? 1 : 0]);
+        } else {
 #pragma unroll
-        for (int k = 0; k < kScanItems; k += 4)
-            *reinterpret_cast<int4 *>(a.bucket_start + base + k) = make_int4(o[k], o[k + 1], o[k + 2], o[k + 3]);
+            for (int k = 0; k < ITEMS; k += 4)
+                *reinterpret_cast<int4 *>(a.bucket_start + base + k) = make_int4(o[k], o[k + 1], o[k + 2], o[k + 3]);
+        }
         return;
     }
 
     // ---- frontier flags -> ascending frontier list (Algorithm 1, Lemma 1)
     const int tp = t;
-    const int base = tp * kScanTile + threadIdx.x * kScanItems;
-    uint32_t f[kScanItems];
+    const int base = tp * TILE + threadIdx.x * ITEMS;
+    uint32_t f[ITEMS];
     uint32_t rho = 0u;                 // bit k: item k flagged by the rho heuristic
-    static_assert(kScanItems <= 32, "rho flags fit one word");
-    int sc[kScanItems];
-    int hc[kScanItems];                // LAT: entropy cell of a frontier item, loaded early
+    static_assert(ITEMS <= 32, "rho flags fit one word");
+    int sc[ITEMS];
+    int hc[ITEMS];                // LAT: entropy cell of a frontier item, loaded early
     uint32_t sum = 0u;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
         const int i = base + k;
         f[k] = 0u;
         sc[k] = -1;
@@ -283,9 +295,9 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     // locally and reduce once per warp; a scene change inside them is flushed directly
     int cur = -1, acc_first = 0, acc_rho = 0;
     double acc_dl = 0.0;
-    int old[kScanItems];               // LAT: the atomics' results, used after all are issued
+    int old[ITEMS];               // LAT: the atomics' results, used after all are issued
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
         const int i = base + k;
         const int s = sc[k];
         old[k] = -1;
@@ -320,7 +332,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
     }
     if (LAT) {
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
+        for (int k = 0; k < ITEMS; ++k) {
             const int s = sc[k];
             if (s < 0) continue;
             if (s != cur) {
@@ -355,18 +367,21 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
 // ============================================================================ k_select
 
 // One CTA per scene: select_scene (cert_phases.cuh) on the scan's results.
-template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_select(const StepArgs a)
+// NT threads per scene: 256 for batches; 1024 for fewer scenes than SMs,
+// where each CTA's chain of dependent steps is the kernel's time and more
+// threads shorten it (one median sample per thread instead of four).
+template <int DIM, int NT>
+__global__ void __launch_bounds__(NT) k_select(const StepArgs a)
 {
     __shared__ SelectSmem sm;
     __shared__ uint32_t s_mot[2][kMotionStride];
     const int s = blockIdx.x;
     const SceneAcc &acc = a.acc[s];
     const int nF = a.fstart[s + 1] - a.fstart[s];
-    select_scene<DIM, kThreads>(a, s, eps_of(a.acc, s), nF, acc.s_front, acc.occ, acc.frontier_cells, sm);
+    select_scene<DIM, NT>(a, s, eps_of(a.acc, s), nF, acc.s_front, acc.occ, acc.frontier_cells, sm);
     if (a.mode == MODE_STEP)   // the refresh's local motion bound (k_scatter_refresh)
         dilate_motion<DIM>(a.mgrid + s * kMotionStride, s_mot[0], s_mot[1], a.mdil + s * kMotionStride,
-                           threadIdx.x, kThreads);
+                           threadIdx.x, NT);
 }
 
 // ============================================================================ k_scatter_refresh
@@ -639,14 +654,15 @@ __device__ void order_chunks(const StepArgs &a, int nch, int *s_hist, int *s_sta
 // merges the 256 partial top-3 lists; the result is exact (every point seen).
 constexpr int kFarCtas = 2 * 148;
 
+// Far queries first, first + stride, ... of the far list, each scanned by the
+// whole CTA (kThreads threads) over its scene; the CTA's warps merge their top-4
+// lists through s_d / s_j.
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) k_far(const StepArgs a)
+__device__ void far_items(const StepArgs &a, int first, int stride, float (*s_d)[4], int (*s_j)[4])
 {
-    __shared__ float s_d[kThreads / 32][4];
-    __shared__ int s_j[kThreads / 32][4];
     const int nfar = *a.far_count;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int item = blockIdx.x; item < nfar; item += gridDim.x) {
+    for (int item = first; item < nfar; item += stride) {
         const int slot = a.far_list[item];
         const int s = a.scene_of[slot];
         const SceneParams sp = a.sp[s];
@@ -696,6 +712,14 @@ __global__ void __launch_bounds__(kThreads) k_far(const StepArgs a)
         }
         __syncthreads();
     }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) k_far(const StepArgs a)
+{
+    __shared__ float s_d[kThreads / 32][4];
+    __shared__ int s_j[kThreads / 32][4];
+    far_items<DIM>(a, blockIdx.x, gridDim.x, s_d, s_j);
 }
 
 // ============================================================================ k_geometry
@@ -808,12 +832,23 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
         break;
     }
     case PH_SCAN:
-        if (a.ntiles_b + a.ntiles_p < kScanLatencyTiles)
-            k_scan<DIM, true><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a);
-        else
-            k_scan<DIM, false><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a);
+        if (a.ntiles_b + a.ntiles_p < kScanLatencyTiles) {
+            // a small grid: latency issue order and quarter tiles (two items per thread),
+            // four times the CTAs and a quarter of each thread's chain
+            StepArgs b = a;
+            b.ntiles_b = a.ntiles_b * (kScanItems / 2);
+            b.ntiles_p = nblk(a.n_total, kThreads * 2);
+            k_scan<DIM, true, 2><<<b.ntiles_b + b.ntiles_p, kThreads, 0, st>>>(b);
+        } else {
+            k_scan<DIM, false, kScanItems><<<a.ntiles_b + a.ntiles_p, kThreads, 0, st>>>(a);
+        }
         break;
-    case PH_SELECT: k_select<DIM><<<a.n_scenes, kThreads, 0, st>>>(a); break;
+    case PH_SELECT:
+        if (a.n_scenes < 148)
+            k_select<DIM, 1024><<<a.n_scenes, 1024, 0, st>>>(a);
+        else
+            k_select<DIM, kThreads><<<a.n_scenes, kThreads, 0, st>>>(a);
+        break;
     case PH_SCATTER:
         if (a.audit & CERT_AUDIT_COST)
             launch_scatter<DIM, true>(a, st);
