@@ -276,10 +276,11 @@ float cert_get_cell_scale(const cert_ctx *ctx);
  *   CERT_PATH_AUTO   (default) the fused step when no scene has more than
  *                    4,096 points or search-grid buckets -- such a scene's
  *                    sorted points and bucket starts then stay in shared
- *                    memory for the whole step -- and either the context
- *                    holds 16 or more scenes or none has more than 2,560
- *                    points; else the multi-kernel step (one CTA per larger
- *                    scene is slower than spreading each phase over the GPU).
+ *                    memory for the whole step -- and either none has more
+ *                    than 2,560 points or the context holds 148 or more
+ *                    scenes (a full wave of one CTA per SM); else the
+ *                    multi-kernel step (one CTA per larger scene is slower
+ *                    than spreading each phase over the GPU).
  * Both paths give the same results bit for bit (every certificate, flag,
  * count and H), except n_searched, which counts the work the refresh left to
  * the search.  cert_set_step_path returns CERT_EINVAL for CERT_PATH_FUSED on a

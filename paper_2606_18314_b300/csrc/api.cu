@@ -232,17 +232,21 @@ static StepArgs make_args(cert_ctx *c, int mode)
 // The fused step (one launch per step, fused_step.cu) runs a step when every
 // scene fits its limits, the strategy is not the all-pairs pass, and either it
 // was asked for or, on CERT_PATH_AUTO, every scene is small enough to keep its
-// sorted points in shared memory -- and, for fewer than kFusedAutoScenes
-// scenes, has at most kFusedAutoSingleN points.  For larger scenes one CTA per
-// scene is a long chain of dependent L2 accesses on one SM, slower than the
-// multi-kernel step that spreads each phase over the GPU (measured: N =
-// 16,000, d = 3, 0.29 vs 0.051 ms per step; the 512-scene batch 1.38 vs
-// 0.65 ms).  A lone scene crosses over between 2,000 and 4,000 points (d = 2:
-// 0.033 vs 0.041 ms at 2,000, 0.056 vs 0.041 ms at 4,000; d = 3: 0.040 vs
-// 0.044 and 0.058 vs 0.046 ms), while batches of 16 or more scenes of at most
-// 4,096 points gain from the fused step at every size measured (512 scenes of
-// 500 to 4,000 points, d = 3: 0.21 vs 0.29 ms).
-constexpr int kFusedAutoScenes = 16;
+// sorted points in shared memory -- and either has at most kFusedAutoSingleN
+// points or the batch holds at least kFusedAutoScenes scenes.  One CTA per
+// scene makes the fused step as long as its largest scene's chain of dependent
+// accesses on one SM, whatever the number of scenes up to one wave, while the
+// multi-kernel step spreads every phase over the GPU and grows with the total.
+// Measured (graph replay, mixed families, scenes log-uniform from 500 points):
+// up to 1,000 or 2,000 points per scene the fused step is 0.53 to 1.01 of the
+// multi-kernel step's time from 16 to 296 scenes; up to 4,000 points it is
+// 1.32 to 1.60 with 16 to 64 scenes, 0.97 to 0.99 with 148 and 0.67 to 0.75
+// with 296.  A lone scene crosses over between 2,000 and 4,000 points (d = 2:
+// 0.033 vs 0.035 ms at 2,000, 0.056 vs 0.035 ms at 4,000; d = 3: 0.042 vs
+// 0.039 and 0.060 vs 0.041 ms).  Larger scenes (N = 16,000, d = 3: 0.29 vs
+// 0.051 ms per step; the 512-scene batch: 1.38 vs 0.65 ms) always take the
+// multi-kernel step.
+constexpr int kFusedAutoScenes = 148;   // one CTA per SM: a full wave of scenes
 constexpr int kFusedAutoSingleN = 2560;
 static bool fused_resident(const cert_ctx *c)
 {
@@ -254,7 +258,7 @@ static bool use_fused(const cert_ctx *c, int strategy)
     if (!c->fused_ok || strategy == STRAT_ALL || c->step_path == CERT_PATH_MULTI) return false;
     if (c->audit & CERT_AUDIT_COST) return false;   // the cost audit instruments the multi-kernel step
     if (c->step_path == CERT_PATH_FUSED) return true;
-    return fused_resident(c) && (c->S >= kFusedAutoScenes || c->max_n <= kFusedAutoSingleN);
+    return fused_resident(c) && (c->max_n <= kFusedAutoSingleN || c->S >= kFusedAutoScenes);
 }
 
 // CTA size of the fused step: 512 threads (two CTAs per SM) for batches that

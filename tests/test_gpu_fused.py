@@ -187,16 +187,18 @@ def test_fused_geometry_audit_matches_oracle(torch):
 
 
 def test_auto_path_rule(torch):
-    """CERT_PATH_AUTO: a lone scene takes the fused step up to 2,560 points;
-    16 or more scenes do while none has more than 4,096 points; larger scenes
-    take the multi-kernel step."""
+    """CERT_PATH_AUTO: scenes of at most 2,560 points take the fused step
+    however many there are; scenes of up to 4,096 points take it in batches of
+    148 or more (a full wave of one CTA per SM); larger scenes take the
+    multi-kernel step."""
     from paper_2606_18314_b300 import cert
     rng = np.random.default_rng(3)
     for n, want in ((2560, "fused"), (2561, "multi"), (4096, "multi")):
         c = cert.Context(torch.from_numpy(rng.random((n, 3)).astype(np.float32)).cuda())
         assert c.step_path("incremental") == want, n
         c.close()
-    for sizes, want in (([4096] * 16, "fused"), ([4096] * 15, "multi"), ([500] * 15 + [4097], "multi")):
+    for sizes, want in (([2560] * 15, "fused"), ([3000] * 148, "fused"), ([3000] * 147, "multi"),
+                        ([500] * 147 + [4096], "fused"), ([500] * 160 + [4097], "multi")):
         off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         c = cert.Context(torch.from_numpy(rng.random((int(off[-1]), 3)).astype(np.float32)).cuda(), offsets=off)
         assert c.step_path("incremental") == want, (len(sizes), max(sizes))
