@@ -91,14 +91,20 @@ struct cert_ctx {
     size_t snap_bytes = 0;
     int snap_cur = 0;
     bool snap_valid = false;
-    // zeroed at the start of every call that runs the pipeline
+    // Counters and accumulators the pipeline's kernels add into.  Zero at the
+    // start of every multi-kernel step: the step's own kernels zero each one
+    // once it is dead (StepArgs::ztail), the fused step leaves them untouched,
+    // and zero_dirty (set by a CUDA error, which may have cut a step short)
+    // makes the next step memset them first.
     char *zero = nullptr;
-    size_t zero_bytes = 0;
+    size_t zero_bytes = 0, ztail_off = 0;
+    bool zero_dirty = true;
     SceneAcc *acc = nullptr;
     uint32_t *tile_ctr = nullptr;
     uint64_t *tstat_b = nullptr, *tstat_p = nullptr;
-    int32_t *bucket_count = nullptr, *hocc = nullptr, *hfail = nullptr, *hcand = nullptr;
-    uint32_t *mgrid = nullptr, *mdil = nullptr;   // motion grid (zeroed every step) and its dilation
+    int32_t *bucket_count = nullptr, *hfail = nullptr, *hcand = nullptr;
+    uint32_t *hocc = nullptr;   // one bit per entropy cell: occupied
+    uint32_t *mgrid = nullptr, *mdil = nullptr;   // motion grid (k_search zeroes it once dilated) and its dilation
     int32_t *chunk_cnt = nullptr, *chunk_order = nullptr;   // batch search: chunk weights and dispatch order
     cudaStream_t last = nullptr;
     bool stepped = false;
@@ -127,6 +133,10 @@ void record_thread_error(const char *msg) { g_err = msg; }
 
 static cert_status cuda_fail(cert_ctx *ctx, const char *what, cudaError_t e)
 {
+    if (ctx) {   // a step may have stopped short of the kernels that zero the counters
+        ctx->zero_dirty = true;
+        ++ctx->settings_epoch;   // and cached step graphs were captured without the memset
+    }
     return fail(ctx, CERT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
@@ -209,6 +219,8 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.fstart = c->fstart;
     a.tstat_b = c->tstat_b;
     a.tstat_p = c->tstat_p;
+    a.ztail = reinterpret_cast<int4 *>(c->zero + c->ztail_off);
+    a.ztail_n16 = (long long)((c->zero_bytes - c->ztail_off) / 16);
     a.tile_ctr = c->tile_ctr;
     a.ntiles_b = c->ntiles_b;
     a.ntiles_p = 0;
@@ -279,6 +291,7 @@ static cert_status run_full(cert_ctx *c, int mode, const float *pos_in, cudaStre
     CK(c, launch_step_phase(a, PH_SEARCH, s));
     CK(c, launch_step_phase(a, PH_SELECT, s));
     CK(c, launch_step_phase(a, PH_FINALIZE, s));
+    c->zero_dirty = false;   // k_search, k_select and k_finalize zeroed what the kernels filled
     // clock rule: every certificate was just recomputed, so the next step's scan
     // revisits every point (resets S_i, c^rev_i and (d1 + d2)^rev_i)
     if (c->frontier_rule == CERT_FRONTIER_CLOCK) CK(c, cudaMemsetAsync(c->inF, 1, size_t(c->N), s));
@@ -446,12 +459,15 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     cv.off = (cv.off + 255) & ~size_t(255);
     const size_t zero_begin = cv.off;
     const size_t o_acc = cv.take<SceneAcc>(S), o_ctr = cv.take<uint32_t>(4), o_farc = cv.take<int32_t>(4),
-                 o_tb = cv.take<uint64_t>(c->ntiles_b * (kScanItems / 2)),
+                 o_hfail = cv.take<int32_t>(hoff);
+    // the span k_search zeroes (StepArgs::ztail)
+    const size_t o_tb = cv.take<uint64_t>(c->ntiles_b * (kScanItems / 2)),
                  o_tp = cv.take<uint64_t>(ceil_div(N, kThreads * 2)),   // small grids scan quarter tiles
-                 o_bcount = cv.take<int32_t>(c->n_buckets_pad), o_hocc = cv.take<int32_t>(hoff),
-                 o_hfail = cv.take<int32_t>(hoff), o_hcand = cv.take<int32_t>(hoff),
-                 o_mgrid = cv.take<uint32_t>(S * kMotionStride);
+                 o_bcount = cv.take<int32_t>(c->n_buckets_pad), o_hocc = cv.take<uint32_t>(hoff / 32 + 1),
+                 o_hcand = cv.take<int32_t>(hoff), o_mgrid = cv.take<uint32_t>(S * kMotionStride);
+    cv.off = (cv.off + 15) & ~size_t(15);
     c->zero_bytes = cv.off - zero_begin;
+    c->ztail_off = o_tb - zero_begin;
     c->blob_bytes = cv.off;
     cudaError_t e = cudaMalloc((void **)&c->blob, c->blob_bytes);
     if (e != cudaSuccess) {
@@ -511,7 +527,7 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     c->tstat_b = (uint64_t *)(b + o_tb);
     c->tstat_p = (uint64_t *)(b + o_tp);
     c->bucket_count = (int32_t *)(b + o_bcount);
-    c->hocc = (int32_t *)(b + o_hocc);
+    c->hocc = (uint32_t *)(b + o_hocc);
     c->hfail = (int32_t *)(b + o_hfail);
     c->hcand = (int32_t *)(b + o_hcand);
 
@@ -610,7 +626,7 @@ cert_status cert_step(cert_ctx *c, const float *d_pos_new, float eps, int32_t st
         return CERT_OK;
     }
     CK(c, mark(0));
-    CK(c, cudaMemsetAsync(c->zero, 0, c->zero_bytes, s));
+    if (c->zero_dirty) CK(c, cudaMemsetAsync(c->zero, 0, c->zero_bytes, s));
     CK(c, mark(1));
     CK(c, launch_step_phase(a, PH_PREPARE, s));
     CK(c, mark(2));
@@ -637,6 +653,8 @@ cert_status cert_step(cert_ctx *c, const float *d_pos_new, float eps, int32_t st
         mo.step_mode = 1;
         mo.step = a;
         CK(c, launch_allpairs_merge(ap, mo, c->N, s));
+        // no k_search on this path: zero its span here
+        CK(c, cudaMemsetAsync(c->zero + c->ztail_off, 0, c->zero_bytes - c->ztail_off, s));
     } else {
         CK(c, launch_step_phase(a, PH_SCATTER, s));
         CK(c, mark(5));
@@ -644,6 +662,7 @@ cert_status cert_step(cert_ctx *c, const float *d_pos_new, float eps, int32_t st
     }
     CK(c, mark(6));
     CK(c, launch_step_phase(a, PH_FINALIZE, s));
+    c->zero_dirty = false;
     CK(c, mark(7));
     CK(c, mark(8));
     c->cur ^= 1;
@@ -683,7 +702,7 @@ static cert_status step_by_graph(cert_ctx *c, const float *stage, int b, float e
         if (!c->capture_stream) CK(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
         const int cur0 = c->cur;
         const cudaStream_t last0 = c->last;
-        const bool stepped0 = c->stepped;
+        const bool stepped0 = c->stepped, dirty0 = c->zero_dirty;
         CK(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
         c->res_target = c->res_ring + (size_t)b * c->S;   // this parity's result slot
         const cert_status rc = cert_step(c, stage, eps, strategy, nullptr, c->capture_stream);
@@ -693,6 +712,7 @@ static cert_status step_by_graph(cert_ctx *c, const float *stage, int b, float e
         c->cur = cur0;              // the capture enqueued nothing: undo its bookkeeping
         c->last = last0;
         c->stepped = stepped0;
+        c->zero_dirty = dirty0;
         if (rc != CERT_OK) {
             if (graph) cudaGraphDestroy(graph);
             return rc;

@@ -41,7 +41,7 @@ struct StepArgs {
     int32_t *chunk_cnt;            // [n_chunks] queries each batch search chunk had (kept for the next step)
     int32_t *chunk_order;          // [n_chunks] the search's CTA -> chunk map, heaviest chunks first
     int order_chunks;              // k_prepare's first CTA orders this many chunks (0: the search is unordered)
-    int32_t *far_count;            // number of entries in far_list (zeroed every call)
+    int32_t *far_count;            // number of entries in far_list (zeroed by k_prepare)
     // certificates
     int frontier_rule;             // cert_frontier_rule
     int audit;                     // cert_audit flags: rho (inF bit 1), geometry (position sums)
@@ -50,13 +50,22 @@ struct StepArgs {
     int32_t *nn, *nn2, *nn3;       // nearest, runner-up, third stored candidate (-1: none)
     float *d1sq, *d2sq, *L;        // L: lower bound on the distance to every other point
     // step outputs
-    int32_t *hcell, *hocc, *hfail, *hcand;
+    int32_t *hcell, *hfail, *hcand;  // entropy cell per point; failures and frontier points per cell
+    uint32_t *hocc;                // occupied entropy cells, one bit per cell (global index h_off + cell)
     uint8_t *inF, *failed;         // inF bit 0: in F_t; bit 1: rho-flagged (CERT_AUDIT_RHO)
     int32_t *frontier, *fstart;
     // chained-scan state
     uint64_t *tstat_b, *tstat_p;
-    uint32_t *tile_ctr;
+    uint32_t *tile_ctr;            // chained scans' tile tickets (zeroed by k_prepare)
     int ntiles_b, ntiles_p;
+    // Counters that k_prepare, k_scan and k_select accumulate (the scan tile
+    // states, bucket counts, occupancy, frontier-cell and motion grids): one
+    // 16-byte-aligned span that k_search zeroes for the next call once they
+    // are dead.  hfail is zeroed per scene by k_select, acc[s] by k_finalize
+    // after reading it; so every call that ends with k_search and k_finalize
+    // leaves them all zero and the next step needs no memset.
+    int4 *ztail;
+    long long ztail_n16;           // 16-byte words of the span
     const double *nlogn;
     cert_scene_result *res;
     float declared_eps;

@@ -503,8 +503,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fused_step(const StepArgs a, 
             acc.f_sum[k] = m.geo[k];
             acc.a_sum[k] = m.geo[4 + k];
         }
-        a.acc[s] = acc;
-        a.fstart[s] = off;
+        a.fstart[s] = off;   // (the global accumulators stay zero: the multi-kernel step's invariant)
         finalize_scene(a, s, acc, nF, off);
     }
 }

@@ -63,6 +63,10 @@ __global__ void __launch_bounds__(kThreads, 5) k_prepare(const StepArgs a)   // 
         __shared__ int s_hist[32], s_start[32];
         order_chunks(a, a.order_chunks, s_hist, s_start);
     }
+    if (blockIdx.x == 0 && threadIdx.x < 4) {   // the scans' tickets and the far list start empty
+        a.tile_ctr[threadIdx.x] = 0u;
+        a.far_count[threadIdx.x] = 0;
+    }
     const int base = blockIdx.x * (kThreads * PER) + threadIdx.x;
     int s[PER];
     float4 p[PER], po[PER];
@@ -126,7 +130,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_prepare(const StepArgs a)   // 
             const int hx = cell_coord(p[k].x, gh, ghf);
             const int hy = cell_coord(p[k].y, gh, ghf);
             hc[k] = (DIM == 3) ? (cell_coord(p[k].z, gh, ghf) * gh + hy) * gh + hx : hy * gh + hx;
-            first[k] = atomicAdd(&a.hocc[sp.h_off + hc[k]], 1) == 0;
+            const int hg = sp.h_off + hc[k];   // the first point to mark the cell counts it
+            const uint32_t bit = 1u << (hg & 31);
+            first[k] = (atomicOr(&a.hocc[hg >> 5], bit) & bit) == 0u;
         }
     }
 #pragma unroll
@@ -379,6 +385,11 @@ __global__ void __launch_bounds__(NT) k_select(const StepArgs a)
     const SceneAcc &acc = a.acc[s];
     const int nF = a.fstart[s + 1] - a.fstart[s];
     select_scene<DIM, NT>(a, s, eps_of(a.acc, s), nF, acc.s_front, acc.occ, acc.frontier_cells, sm);
+    {   // the scene's failure histogram starts empty (the refresh, search and far pass fill it)
+        const SceneParams sp = a.sp[s];
+        const int cells = (DIM == 3) ? sp.g_h * sp.g_h * sp.g_h : sp.g_h * sp.g_h;
+        for (int k = threadIdx.x; k < cells; k += NT) a.hfail[sp.h_off + k] = 0;
+    }
     if (a.mode == MODE_STEP)   // the refresh's local motion bound (k_scatter_refresh)
         dilate_motion<DIM>(a.mgrid + s * kMotionStride, s_mot[0], s_mot[1], a.mdil + s * kMotionStride,
                            threadIdx.x, NT);
@@ -617,6 +628,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
             r0 += NQ;
         }
     }
+    // the counters of the earlier phases are dead: zero them for the next call,
+    // each warp once it has no query left (stores only)
+    for (long long w = (long long)blockIdx.x * kThreads + threadIdx.x; w < a.ztail_n16;
+         w += (long long)gridDim.x * kThreads)
+        a.ztail[w] = make_int4(0, 0, 0, 0);
 }
 
 // ============================================================================ chunk order
@@ -761,12 +777,15 @@ __global__ void __launch_bounds__(kThreads) k_geometry(const StepArgs a)
 
 // ============================================================================ k_finalize
 
-// One thread per scene: finalize_scene (cert_phases.cuh).
+// One thread per scene: finalize_scene (cert_phases.cuh); the scene's
+// accumulators are then zeroed for the next call.
 __global__ void k_finalize(const StepArgs a)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.n_scenes) return;
-    finalize_scene(a, s, a.acc[s], a.fstart[s + 1] - a.fstart[s], a.fstart[s]);
+    const SceneAcc acc = a.acc[s];
+    finalize_scene(a, s, acc, a.fstart[s + 1] - a.fstart[s], a.fstart[s]);
+    a.acc[s] = SceneAcc{};
 }
 
 // ============================================================================ distances
