@@ -292,7 +292,7 @@ __global__ void k_allpairs_merge_step(const APArgs a, const APMergeOut o)
             const uint32_t fl = sa.inF[i];   // bit 0: in F_t, bit 1: rho-flagged
             missed = !(fl & 1u);
             hit = (int)(fl >> 1);
-            const int old = atomicAdd(&sa.hfail[sp.h_off + sa.hcell[i]], 1);
+            const int old = count_inc(sa.hfail, sp.h_off + sa.hcell[i], sa.c16h);
             first = old == 0;
             dl = nlogn_step(sa.nlogn, old);
         }

@@ -86,6 +86,7 @@ struct cert_ctx {
     bool fused_ok = false;
     int step_path = CERT_PATH_AUTO;
     int max_n = 0, max_T = 0;
+    bool c16b = false, c16h = false;   // 16-bit bucket counts; 16-bit entropy-cell counts
     int32_t *order = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
     size_t snap_bytes = 0;
@@ -213,6 +214,8 @@ static StepArgs make_args(cert_ctx *c, int mode)
     a.hocc = c->hocc;
     a.hfail = c->hfail;
     a.hcand = c->hcand;
+    a.c16b = c->c16b ? 1 : 0;
+    a.c16h = c->c16h ? 1 : 0;
     a.inF = c->inF;
     a.failed = c->failed;
     a.frontier = c->frontier;
@@ -258,6 +261,7 @@ static StepArgs make_args(cert_ctx *c, int mode)
 // 0.039 and 0.060 vs 0.041 ms).  Larger scenes (N = 16,000, d = 3: 0.29 vs
 // 0.051 ms per step; the 512-scene batch: 1.38 vs 0.65 ms) always take the
 // multi-kernel step.
+constexpr int64_t kC16MinN = 262144;
 constexpr int kFusedAutoScenes = 148;   // one CTA per SM: a full wave of scenes
 constexpr int kFusedAutoSingleN = 2560;
 static bool fused_resident(const cert_ctx *c)
@@ -406,8 +410,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
         p.bucket_mask = T - 1;
         boff += T;
         p.g_h = entropy_res(n, c->dim);
-        p.h_off = (int32_t)hoff;
-        hoff += (int64_t)std::pow((double)p.g_h, (double)c->dim) + 0.5;
+        p.h_off = (int32_t)hoff;   // a multiple of 8 (16-bit counts: 16-byte words of its own)
+        hoff += ((int64_t)(std::pow((double)p.g_h, (double)c->dim) + 0.5) + 7) & ~int64_t(7);
         p.g_default = std::max(1, (int)std::floor(std::pow(n / 2.0, 1.0 / c->dim)));
         const int nch = (int)std::min<int64_t>(nch_all, ceil_div(n, 256));
         p.ap_nch = nch;
@@ -427,6 +431,12 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
         c->max_T = std::max(c->max_T, (int)p.bucket_mask + 1);
         if (p.n > kFusedMaxN || p.bucket_mask + 1 > kFusedMaxBuckets || cells > kFusedMaxHCells) c->fused_ok = false;
     }
+    // 16-bit counts (no scene reaches 65,536 points, so no count reaches 2^16)
+    // for contexts of more than kC16MinN points, where the arrays' footprint
+    // matters more than two counters sharing an atomic's word (measured: the
+    // 512-scene batch 4.44e9 -> 4.48e9 point-updates/s; a lone scene of 16,000
+    // points, whose atomics are its step's critical chain, 0.045 -> 0.047 ms)
+    c->c16b = c->c16h = c->max_n < 65536 && c->N > kC16MinN;
     c->n_buckets = (int)boff;
     c->n_buckets_pad = (int)ceil_div(boff + 1, kScanTile) * kScanTile;
     c->ntiles_b = c->n_buckets_pad / kScanTile;
@@ -459,12 +469,13 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     cv.off = (cv.off + 255) & ~size_t(255);
     const size_t zero_begin = cv.off;
     const size_t o_acc = cv.take<SceneAcc>(S), o_ctr = cv.take<uint32_t>(4), o_farc = cv.take<int32_t>(4),
-                 o_hfail = cv.take<int32_t>(hoff);
+                 o_hfail = cv.take<int32_t>(c->c16h ? hoff / 2 : hoff);
     // the span k_search zeroes (StepArgs::ztail)
     const size_t o_tb = cv.take<uint64_t>(c->ntiles_b * (kScanItems / 2)),
                  o_tp = cv.take<uint64_t>(ceil_div(N, kThreads * 2)),   // small grids scan quarter tiles
-                 o_bcount = cv.take<int32_t>(c->n_buckets_pad), o_hocc = cv.take<uint32_t>(hoff / 32 + 1),
-                 o_hcand = cv.take<int32_t>(hoff), o_mgrid = cv.take<uint32_t>(S * kMotionStride);
+                 o_bcount = cv.take<int32_t>(c->c16b ? c->n_buckets_pad / 2 : c->n_buckets_pad),
+                 o_hocc = cv.take<uint32_t>(hoff / 32 + 1), o_hcand = cv.take<int32_t>(c->c16h ? hoff / 2 : hoff),
+                 o_mgrid = cv.take<uint32_t>(S * kMotionStride);
     cv.off = (cv.off + 15) & ~size_t(15);
     c->zero_bytes = cv.off - zero_begin;
     c->ztail_off = o_tb - zero_begin;

@@ -527,6 +527,19 @@ constexpr unsigned kFull = 0xffffffffu;
 // Lanes of a warp holding consecutive points form contiguous runs of equal
 // scene id (scenes are contiguous ranges).  Each helper reduces within the run
 // and lets the run's lowest lane issue one atomic.  s < 0 marks an idle lane.
+// Increment counter k of a per-bucket or per-entropy-cell count array and
+// return its previous value.  c16: the counts are 16-bit, two per word (every
+// scene has fewer than 65,536 points, so no count reaches 2^16 and the low
+// half never carries into the high one); otherwise one 32-bit count per entry.
+__device__ __forceinline__ int count_inc(int32_t *arr, int k, int c16)
+{
+    if (c16) {
+        const uint32_t sh = (uint32_t)(k & 1) << 4;
+        return (int)((atomicAdd(reinterpret_cast<uint32_t *>(arr) + (k >> 1), 1u << sh) >> sh) & 0xffffu);
+    }
+    return atomicAdd(arr + k, 1);
+}
+
 __device__ __forceinline__ unsigned scene_run_mask(int s)
 {
     return __match_any_sync(kFull, s);

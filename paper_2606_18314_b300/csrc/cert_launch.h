@@ -51,6 +51,7 @@ struct StepArgs {
     float *d1sq, *d2sq, *L;        // L: lower bound on the distance to every other point
     // step outputs
     int32_t *hcell, *hfail, *hcand;  // entropy cell per point; failures and frontier points per cell
+    int c16b, c16h;                // 16-bit counts (count_inc): bucket_count; hfail and hcand
     uint32_t *hocc;                // occupied entropy cells, one bit per cell (global index h_off + cell)
     uint8_t *inF, *failed;         // inF bit 0: in F_t; bit 1: rho-flagged (CERT_AUDIT_RHO)
     int32_t *frontier, *fstart;

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_prepare(const StepArgs a)   // 
         const int cz = (DIM == 3) ? cell_coord(p[k].z, g, gf) : 0;
         const bool dense = grid_is_dense<DIM>(g, sp.bucket_mask + 1);
         b[k] = sp.bucket_off + (int)((row_base<DIM>(cy, cz, g, dense) + (uint32_t)cx) & (uint32_t)sp.bucket_mask);
-        rank[k] = atomicAdd(&a.bucket_count[b[k]], 1);
+        rank[k] = count_inc(a.bucket_count, b[k], a.c16b);
         // the motion grid of the refresh's local bound (static points add nothing)
         // (read first: cells of dense scenes take hundreds of points, and their
         // maximum is reached early, so most of the atomics would serialise for nothing)
@@ -207,7 +207,7 @@ template <int DIM, bool LAT, int ITEMS>
 __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
 {
     constexpr int TILE = kThreads * ITEMS;
-    static_assert(ITEMS == 2 || ITEMS % 4 == 0, "bucket counts load two or four at a time");
+    static_assert(ITEMS == 2 || ITEMS % 8 == 0, "bucket counts load two, or four / eight (c16) at a time");
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ int s_tile;
     __shared__ uint32_t s_excl;
@@ -223,7 +223,27 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
         const int tb = t - a.ntiles_p;
         const int base = tb * TILE + threadIdx.x * ITEMS;
         uint32_t v[ITEMS];
-        if constexpr (ITEMS == 2) {
+        if (a.c16b) {   // 16-bit counts: ITEMS of them in ITEMS / 2 words
+            const uint16_t *c16 = reinterpret_cast<const uint16_t *>(a.bucket_count) + base;
+            if constexpr (ITEMS == 2) {
+                const uint32_t w = *reinterpret_cast<const uint32_t *>(c16);
+                v[0] = w & 0xffffu;
+                v[ITEMS > 1 ? 1 : 0] = w >> 16;
+            } else {
+#pragma unroll
+                for (int k = 0; k < ITEMS; k += 8) {
+                    const uint4 w = *reinterpret_cast<const uint4 *>(c16 + k);
+                    v[k] = w.x & 0xffffu;
+                    v[k + 1] = w.x >> 16;
+                    v[k + 2] = w.y & 0xffffu;
+                    v[k + 3] = w.y >> 16;
+                    v[k + 4] = w.z & 0xffffu;
+                    v[k + 5] = w.z >> 16;
+                    v[k + 6] = w.w & 0xffffu;
+                    v[k + 7] = w.w >> 16;
+                }
+            }
+        } else if constexpr (ITEMS == 2) {
             const int2 c2 = *reinterpret_cast<const int2 *>(a.bucket_count + base);
             v[0] = (uint32_t)c2.x;
             v[ITEMS > 1 ? 1 : 0] = (uint32_t)c2.y;
@@ -325,9 +345,9 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
             if (f[k]) {
                 if (run < (uint32_t)a.n_total) a.frontier[run] = i - sp.pt_off;
                 if (LAT) {
-                    old[k] = atomicAdd(&a.hcand[sp.h_off + hc[k]], 1);
+                    old[k] = count_inc(a.hcand, sp.h_off + hc[k], a.c16h);
                 } else {
-                    const int o = atomicAdd(&a.hcand[sp.h_off + a.hcell[i]], 1);
+                    const int o = count_inc(a.hcand, sp.h_off + a.hcell[i], a.c16h);
                     acc_first += o == 0;
                     acc_dl += nlogn_step(a.nlogn, o);
                 }
@@ -388,7 +408,10 @@ __global__ void __launch_bounds__(NT) k_select(const StepArgs a)
     {   // the scene's failure histogram starts empty (the refresh, search and far pass fill it)
         const SceneParams sp = a.sp[s];
         const int cells = (DIM == 3) ? sp.g_h * sp.g_h * sp.g_h : sp.g_h * sp.g_h;
-        for (int k = threadIdx.x; k < cells; k += NT) a.hfail[sp.h_off + k] = 0;
+        // (h_off is a multiple of 8: with 16-bit counts the scene's words are its own)
+        const int w0 = a.c16h ? sp.h_off / 2 : sp.h_off;
+        const int nw = a.c16h ? (cells + 1) / 2 : cells;
+        for (int k = threadIdx.x; k < nw; k += NT) a.hfail[w0 + k] = 0;
     }
     if (a.mode == MODE_STEP)   // the refresh's local motion bound (k_scatter_refresh)
         dilate_motion<DIM>(a.mgrid + s * kMotionStride, s_mot[0], s_mot[1], a.mdil + s * kMotionStride,
@@ -456,7 +479,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
                 const uint32_t fl = a.inF[i];
                 missed[k] = !(fl & 1u);
                 hit[k] = (int)(fl >> 1);
-                const int old = atomicAdd(&a.hfail[sp.h_off + a.hcell[i]], 1);
+                const int old = count_inc(a.hfail, sp.h_off + a.hcell[i], a.c16h);
                 first[k] = old == 0;
                 dl[k] = nlogn_step(a.nlogn, old);
             }
@@ -591,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
             if (gl == 0) {   // the group's lanes hold the same result; one writes it
                 if (ok)
                     o = write_certificate(a, sp, gi, t, L,
-                                          [&](int hc) { return atomicAdd(&a.hfail[sp.h_off + hc], 1); });
+                                          [&](int hc) { return count_inc(a.hfail, sp.h_off + hc, a.c16h); });
                 else
                     a.far_list[atomicAdd(a.far_count, 1)] = slot;   // finished by k_far
             }
@@ -717,7 +740,7 @@ __device__ void far_items(const StepArgs &a, int first, int stride, float (*s_d)
                 for (int k = 0; k < 4; ++k)
                     if (s_j[w][k] != 0x7fffffff) top4_insert(r, s_d[w][k], s_j[w][k]);
             const SearchOut o = write_certificate(a, sp, gi, r, sqrt_lower(r.d3),
-                                                  [&](int hc) { return atomicAdd(&a.hfail[sp.h_off + hc], 1); });
+                                                  [&](int hc) { return count_inc(a.hfail, sp.h_off + hc, a.c16h); });
             if (a.mode == MODE_STEP && o.changed) {
                 atomicAdd(&a.acc[s].n_failed, 1);
                 atomicAdd(&a.acc[s].n_missed, o.missed);
