@@ -3,8 +3,10 @@ its kernels check, at run time, the indices the release build relies on by
 construction (search ranges inside their scene, neighbour indices written
 into certificates, the kNN slot ranges and lists) and would return
 CERT_EINTERNAL on a violation.  The workloads below -- a mixed batch under
-every strategy, the kNN search with its far and heavy paths, the all-pairs
-pass -- must finish with CERT_OK and match the oracle.  Runs in a child
+every strategy, a batch large enough for 16-bit counts, the kNN search with
+its far and heavy paths, the all-pairs pass -- must finish with CERT_OK and
+match the oracle (the 16-bit batch: the all-pairs pass, itself checked
+against the oracle).  Runs in a child
 process, which loads the debug library instead of the release one."""
 import os
 import subprocess
@@ -39,6 +41,19 @@ ctx.rebuild()
 _, rc = ctx.sync(raise_on_status=False)
 assert rc == cert.CERT_OK
 ctx.close()
+# a context of more than 262,144 points with every scene below 65,536: 16-bit counts
+mb = scenes.BatchMotion([scenes.Motion("uniform_clusters", 60000, 3, 1e-3, seed=60 + k, steps=8) for k in range(5)])
+ob, fb = mb.offsets, mb.frames(3)
+cb = cert.Context(torch.from_numpy(fb[0]).cuda(), offsets=ob)
+for t, strat in enumerate(["incremental", "allpairs", "incremental"], start=1):
+    cb.step(torch.from_numpy(fb[t]).cuda(), 1e-3, strat)
+    _, rc = cb.sync(raise_on_status=False)
+    assert rc == cert.CERT_OK, ("16-bit counts", t, cert.STATUS_NAMES[rc])
+    nn = cb.views()["nn"].cpu().numpy()
+    for s in range(5):
+        ref = cert.cert_allpairs(torch.from_numpy(fb[t][ob[s]:ob[s + 1]]).cuda())[0].cpu().numpy()
+        assert np.array_equal(nn[ob[s]:ob[s + 1]], ref), ("16-bit counts", t, s)
+cb.close()
 mk = scenes.Motion("uniform_clusters", 6000, 3, 1e-3, seed=2, steps=20)
 fk = mk.frames(3)
 for scale in (0.05, 1.0, 3.0):
