@@ -259,9 +259,8 @@ static StepArgs make_args(cert_ctx *c, int mode)
 // with 296.  A lone scene crosses over between 2,000 and 4,000 points (d = 2:
 // 0.033 vs 0.035 ms at 2,000, 0.056 vs 0.035 ms at 4,000; d = 3: 0.042 vs
 // 0.039 and 0.060 vs 0.041 ms).  Larger scenes (N = 16,000, d = 3: 0.29 vs
-// 0.051 ms per step; the 512-scene batch: 1.38 vs 0.65 ms) always take the
+// 0.044 ms per step; the 512-scene batch: 1.38 vs 0.65 ms) always take the
 // multi-kernel step.
-constexpr int64_t kC16MinN = 262144;
 constexpr int kFusedAutoScenes = 148;   // one CTA per SM: a full wave of scenes
 constexpr int kFusedAutoSingleN = 2560;
 static bool fused_resident(const cert_ctx *c)
@@ -280,6 +279,10 @@ static bool use_fused(const cert_ctx *c, int strategy)
 // CTA size of the fused step: 512 threads (two CTAs per SM) for batches that
 // fill the GPU, 1024 for fewer scenes than SMs (more threads per scene).
 static int fused_block(const cert_ctx *c) { return c->S >= 148 ? 512 : 1024; }
+
+// Contexts of more than this many points keep 16-bit counts when their scenes
+// allow it (cert_init).
+constexpr int64_t kC16MinN = 262144;
 
 // Grid build + full search of every point of the current positions
 // (initial certificates and cert_rebuild).
