@@ -529,6 +529,15 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
 // lanes per query: the GPU has lanes to spare there, and each lane walks a
 // quarter of its query's quads, which cuts the chain of dependent loads that
 // bounds a lone query's latency.
+// This CTA's share of a grid-stride zeroing of n16 16-byte words.  A call of
+// its own: inlined at the end of k_search, its loop raised the search's spill
+// loads from 44 to 100 bytes per thread.
+__device__ __noinline__ void zero_span(int4 *p, long long n16)
+{
+    for (long long w = (long long)blockIdx.x * kThreads + threadIdx.x; w < n16; w += (long long)gridDim.x * kThreads)
+        p[w] = make_int4(0, 0, 0, 0);
+}
+
 template <int DIM, int CHUNK, int G, bool COST>
 __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 64 registers: 4 CTAs per SM
 {
@@ -653,9 +662,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
     }
     // the counters of the earlier phases are dead: zero them for the next call,
     // each warp once it has no query left (stores only)
-    for (long long w = (long long)blockIdx.x * kThreads + threadIdx.x; w < a.ztail_n16;
-         w += (long long)gridDim.x * kThreads)
-        a.ztail[w] = make_int4(0, 0, 0, 0);
+    zero_span(a.ztail, a.ztail_n16);
 }
 
 // ============================================================================ chunk order
