@@ -494,3 +494,71 @@ def test_pipelined_host_steps_match_the_oracle(torch):
         assert ctx.views() is not None
     with pytest.raises(cert.CertError):
         ctx.step_host_stream([0], 2e-3, cert.CERT_INCREMENTAL, None)
+
+
+def test_every_call_kind_on_one_context_matches_the_oracle(torch):
+    """The step's counters and accumulators are zeroed by its own kernels, so
+    each call must leave them zero for the next: device steps on the
+    multi-kernel and fused paths, the all-pairs and rebuild strategies,
+    cert_rebuild, snapshot / restore, and pipelined host steps replaying cached
+    graphs, interleaved on one context.  After every call each scene matches
+    the oracle (certificates, frontier, failures, cells, H)."""
+    from paper_2606_18314_b300 import cert
+    bm = scenes.BatchMotion.mixed(n_scenes=6, lo=400, hi=3000, eps=2e-3, seed=77)
+    off, fr = bm.offsets, bm.frames(12)
+    S = len(off) - 1
+    host_frames = torch.from_numpy(fr).pin_memory()
+    row = fr[0].size * 4
+    ctx = cert.Context(dev(torch, fr[0]), offsets=off, audit=("rho", "geometry"))
+    refs = [oracle.top2(fr[0][off[s]:off[s + 1]]) for s in range(S)]
+    pos = 0   # frame the context's positions sit at
+
+    def check_step(k, res, tag):
+        nonlocal pos
+        views = ctx.views()
+        for s in range(S):
+            r = oracle.step(fr[pos][off[s]:off[s + 1]], fr[k][off[s]:off[s + 1]], refs[s])
+            assert_step_equal(ctx, res, views, r, s=s, tag=f"{tag} scene {s}")
+            refs[s] = r.cert
+        pos = k
+
+    def device_step(k, strat, path):
+        ctx.set_step_path(path)
+        ctx.step(dev(torch, fr[k]), 2e-3, strat)
+        res, rc = ctx.sync()
+        assert rc == cert.CERT_OK
+        check_step(k, res, f"{path} {strat} frame {k}")
+
+    device_step(1, "incremental", "multi")
+    device_step(2, "allpairs", "auto")
+    device_step(3, "incremental", "fused")
+    device_step(4, "rebuild", "multi")
+    ctx.rebuild()
+    res, rc = ctx.sync()
+    assert rc == cert.CERT_OK
+    nn = host(ctx.views()["nn"])
+    for s in range(S):
+        assert np.array_equal(nn[off[s]:off[s + 1]], refs[s].nn)
+    ctx.snapshot()
+    device_step(5, "incremental", "multi")
+    ctx.restore()   # back at frame 4: step to frame 5 again, then on
+    pos, refs[:] = 4, [oracle.top2(fr[4][off[s]:off[s + 1]]) for s in range(S)]
+    device_step(5, "incremental", "fused")
+    device_step(6, "incremental", "multi")
+    order = [7, 8, 9]
+    out = np.zeros(len(order) * S, cert.SCENE_DTYPE)
+    ctx.set_step_path("multi")
+    ctx.step_host_stream([host_frames.data_ptr() + k * row for k in order], 2e-3, cert.CERT_INCREMENTAL, out)
+    for step, k in enumerate(order):
+        for s in range(S):
+            r = oracle.step(fr[pos][off[s]:off[s + 1]], fr[k][off[s]:off[s + 1]], refs[s])
+            sc = out[step * S + s]
+            assert int(sc["n_failed"]) == r.n_failed and int(sc["n_frontier"]) == len(r.frontier), (k, s)
+            assert int(sc["failed_cells"]) == r.m and int(sc["occupied_cells"]) == r.C, (k, s)
+            assert abs(float(sc["H"]) - r.H) <= H_TOL, (k, s)
+            refs[s] = r.cert
+        pos = k
+    device_step(10, "allpairs", "auto")
+    device_step(11, "incremental", "multi")
+    device_step(12, "incremental", "fused")
+    ctx.close()
