@@ -531,47 +531,62 @@ __device__ __forceinline__ void visit_quad_rows(const SearchCtx &c, const int2 *
     }
 }
 
-// The same walk shared by G lanes of one query: lane g (0 <= g < G) takes the
-// quads g, g + G, ... of every row, with its next quad's loads issued before
-// the current quad's arithmetic.  The lanes' top-4 lists are merged afterwards.
+// The same walk shared by G lanes of one query.  The query's rows are taken as
+// one sequence of quads, and lane g (0 <= g < G) takes quads g, g + G, g + 2G,
+// ... of it, so the lanes' shares differ by at most one quad whatever the row
+// lengths (the group's merge waits for its slowest lane); each lane's next
+// quad's loads are issued before the current quad's arithmetic, across row
+// ends too.  The lanes' top-4 lists are merged afterwards.
 template <int DIM, int STRIDE, int G>
 __device__ __forceinline__ void visit_quad_rows_split(const SearchCtx &c, const int2 *rng, int NR, Top4 &t, int g)
 {
-    for (int k = 0; k < NR; ++k) {
-        const int2 rr = rng[k * STRIDE];
 #ifdef CERT_DEBUG_BOUNDS
-        const int qmin = (c.pt_off + c.pad) >> 2, qmax = (c.pt_off + c.n + c.pad + 3) >> 2;
-        CERT_CHECK(c.status, rr.x >= rr.y || (rr.x >= qmin && rr.y <= qmax));
+    const int qmin = (c.pt_off + c.pad) >> 2, qmax = (c.pt_off + c.n + c.pad + 3) >> 2;
+    for (int kk = 0; kk < NR; ++kk) {
+        const int2 rk = rng[kk * STRIDE];
+        CERT_CHECK(c.status, rk.x >= rk.y || (rk.x >= qmin && rk.y <= qmax));
+    }
 #endif
-        int q = rr.x + g;
-        if (q >= rr.y) continue;
-        const float4 *r = c.squad + (size_t)q * 4;
-        float4 X = r[0], Y = r[1];
-        float4 Z = (DIM == 3) ? r[2] : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (;;) {
-            const float4 cX = X, cY = Y, cZ = Z;
-            const float4 *rc = r;
-            q += G;
-            const bool more = q < rr.y;
-            if (more) {
-                r = c.squad + (size_t)q * 4;
-                X = r[0];
-                Y = r[1];
-                if (DIM == 3) Z = r[2];
-            }
-            float D0, D1, D2, D3;
-            sqdist_quad<DIM>(c.px2, c.py2, c.pz2, cX, cY, cZ, D0, D1, D2, D3);
-            if (fminf(fminf(D0, D1), fminf(D2, D3)) <= t.d3) {
-                const float4 J = rc[3];
-                const int j0 = __float_as_int(J.x), j1 = __float_as_int(J.y);
-                const int j2 = __float_as_int(J.z), j3 = __float_as_int(J.w);
-                if (D0 <= t.d3 && j0 != c.gi) top4_insert(t, D0, j0);
-                if (D1 <= t.d3 && j1 != c.gi) top4_insert(t, D1, j1);
-                if (D2 <= t.d3 && j2 != c.gi) top4_insert(t, D2, j2);
-                if (D3 <= t.d3 && j3 != c.gi) top4_insert(t, D3, j3);
-            }
-            if (!more) break;
+    int k = 0;
+    int2 rr = rng[0];
+    int off = g;   // this lane's position in row k, in quads
+    while (off >= rr.y - rr.x && k + 1 < NR) {
+        off -= max(rr.y - rr.x, 0);
+        ++k;
+        rr = rng[k * STRIDE];
+    }
+    if (off >= rr.y - rr.x) return;   // the rows hold no more than g quads
+    const float4 *r = c.squad + (size_t)(rr.x + off) * 4;
+    float4 X = r[0], Y = r[1];
+    float4 Z = (DIM == 3) ? r[2] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (;;) {
+        const float4 cX = X, cY = Y, cZ = Z;
+        const float4 *rc = r;
+        off += G;
+        while (off >= rr.y - rr.x && k + 1 < NR) {
+            off -= max(rr.y - rr.x, 0);
+            ++k;
+            rr = rng[k * STRIDE];
         }
+        const bool more = off < rr.y - rr.x;
+        if (more) {
+            r = c.squad + (size_t)(rr.x + off) * 4;
+            X = r[0];
+            Y = r[1];
+            if (DIM == 3) Z = r[2];
+        }
+        float D0, D1, D2, D3;
+        sqdist_quad<DIM>(c.px2, c.py2, c.pz2, cX, cY, cZ, D0, D1, D2, D3);
+        if (fminf(fminf(D0, D1), fminf(D2, D3)) <= t.d3) {
+            const float4 J = rc[3];
+            const int j0 = __float_as_int(J.x), j1 = __float_as_int(J.y);
+            const int j2 = __float_as_int(J.z), j3 = __float_as_int(J.w);
+            if (D0 <= t.d3 && j0 != c.gi) top4_insert(t, D0, j0);
+            if (D1 <= t.d3 && j1 != c.gi) top4_insert(t, D1, j1);
+            if (D2 <= t.d3 && j2 != c.gi) top4_insert(t, D2, j2);
+            if (D3 <= t.d3 && j3 != c.gi) top4_insert(t, D3, j3);
+        }
+        if (!more) break;
     }
 }
 
