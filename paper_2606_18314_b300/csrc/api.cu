@@ -474,8 +474,8 @@ cert_status cert_init(cert_ctx **out, const cert_config *cfg, const float *d_pos
     const size_t o_acc = cv.take<SceneAcc>(S), o_ctr = cv.take<uint32_t>(4), o_farc = cv.take<int32_t>(4),
                  o_hfail = cv.take<int32_t>(c->c16h ? hoff / 2 : hoff);
     // the span k_search zeroes (StepArgs::ztail)
-    const size_t o_tb = cv.take<uint64_t>(c->ntiles_b * (kScanItems / 2)),
-                 o_tp = cv.take<uint64_t>(ceil_div(N, kThreads * 2)),   // small grids scan quarter tiles
+    const size_t o_tb = cv.take<uint64_t>(c->ntiles_b * kScanItems),
+                 o_tp = cv.take<uint64_t>(ceil_div(N, kThreads)),   // small grids scan eighth tiles
                  o_bcount = cv.take<int32_t>(c->c16b ? c->n_buckets_pad / 2 : c->n_buckets_pad),
                  o_hocc = cv.take<uint32_t>(hoff / 32 + 1), o_hcand = cv.take<int32_t>(c->c16h ? hoff / 2 : hoff),
                  o_mgrid = cv.take<uint32_t>(S * kMotionStride);

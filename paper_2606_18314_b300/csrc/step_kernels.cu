@@ -207,7 +207,7 @@ template <int DIM, bool LAT, int ITEMS>
 __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
 {
     constexpr int TILE = kThreads * ITEMS;
-    static_assert(ITEMS == 2 || ITEMS % 8 == 0, "bucket counts load two, or four / eight (c16) at a time");
+    static_assert(ITEMS <= 2 || ITEMS % 8 == 0, "bucket counts load one, two, or four / eight (c16) at a time");
     __shared__ uint32_t s_warp[kThreads / 32];
     __shared__ int s_tile;
     __shared__ uint32_t s_excl;
@@ -223,7 +223,10 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
         const int tb = t - a.ntiles_p;
         const int base = tb * TILE + threadIdx.x * ITEMS;
         uint32_t v[ITEMS];
-        if (a.c16b) {   // 16-bit counts: ITEMS of them in ITEMS / 2 words
+        if constexpr (ITEMS == 1) {
+            v[0] = a.c16b ? (uint32_t)reinterpret_cast<const uint16_t *>(a.bucket_count)[base]
+                          : (uint32_t)a.bucket_count[base];
+        } else if (a.c16b) {   // 16-bit counts: ITEMS of them in ITEMS / 2 words
             const uint16_t *c16 = reinterpret_cast<const uint16_t *>(a.bucket_count) + base;
             if constexpr (ITEMS == 2) {
                 const uint32_t w = *reinterpret_cast<const uint32_t *>(c16);
@@ -274,7 +277,9 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
             o[k] = (int)run;
             run += v[k];
         }
-        if constexpr (ITEMS == 2) {
+        if constexpr (ITEMS == 1) {
+            a.bucket_start[base] = o[0];
+        } else if constexpr (ITEMS == 2) {
             *reinterpret_cast<int2 *>(a.bucket_start + base) = make_int2(o[0], o[ITEMS > 1 ? 1 : 0]);
         } else {
 #pragma unroll
@@ -881,7 +886,14 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
         break;
     }
     case PH_SCAN:
-        if (a.ntiles_b + a.ntiles_p < kScanLatencyTiles) {
+        if ((a.ntiles_b + a.ntiles_p) * kScanItems <= 2 * 148) {
+            // a very small grid (a single scene of up to about 18,000 points): eighth
+            // tiles, one item per thread, still at most two CTAs per SM
+            StepArgs b = a;
+            b.ntiles_b = a.ntiles_b * kScanItems;
+            b.ntiles_p = nblk(a.n_total, kThreads);
+            k_scan<DIM, true, 1><<<b.ntiles_b + b.ntiles_p, kThreads, 0, st>>>(b);
+        } else if (a.ntiles_b + a.ntiles_p < kScanLatencyTiles) {
             // a small grid: latency issue order and quarter tiles (two items per thread),
             // four times the CTAs and a quarter of each thread's chain
             StepArgs b = a;
