@@ -401,15 +401,22 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
 // NT threads per scene: 256 for batches; 1024 for fewer scenes than SMs,
 // where each CTA's chain of dependent steps is the kernel's time and more
 // threads shorten it (one median sample per thread instead of four).
-template <int DIM, int NT>
+// SPLIT (fewer scenes than SMs): 2 x n_scenes CTAs; the second n_scenes zero
+// the scenes' failure counts and dilate their motion grids, in parallel with
+// the selections instead of after them.
+template <int DIM, int NT, bool SPLIT>
 __global__ void __launch_bounds__(NT) k_select(const StepArgs a)
 {
     __shared__ SelectSmem sm;
     __shared__ uint32_t s_mot[2][kMotionStride];
-    const int s = blockIdx.x;
-    const SceneAcc &acc = a.acc[s];
-    const int nF = a.fstart[s + 1] - a.fstart[s];
-    select_scene<DIM, NT>(a, s, eps_of(a.acc, s), nF, acc.s_front, acc.occ, acc.frontier_cells, sm);
+    const bool sel = !SPLIT || (int)blockIdx.x < a.n_scenes;   // uniform in the CTA
+    const int s = sel ? (int)blockIdx.x : (int)blockIdx.x - a.n_scenes;
+    if (sel) {
+        const SceneAcc &acc = a.acc[s];
+        const int nF = a.fstart[s + 1] - a.fstart[s];
+        select_scene<DIM, NT>(a, s, eps_of(a.acc, s), nF, acc.s_front, acc.occ, acc.frontier_cells, sm);
+        if (SPLIT) return;
+    }
     {   // the scene's failure histogram starts empty (the refresh, search and far pass fill it)
         const SceneParams sp = a.sp[s];
         const int cells = (DIM == 3) ? sp.g_h * sp.g_h * sp.g_h : sp.g_h * sp.g_h;
@@ -906,9 +913,9 @@ static cudaError_t run_step_dim(const StepArgs &a, int phase, cudaStream_t st)
         break;
     case PH_SELECT:
         if (a.n_scenes < 148)
-            k_select<DIM, 1024><<<a.n_scenes, 1024, 0, st>>>(a);
+            k_select<DIM, 1024, true><<<2 * a.n_scenes, 1024, 0, st>>>(a);
         else
-            k_select<DIM, kThreads><<<a.n_scenes, kThreads, 0, st>>>(a);
+            k_select<DIM, kThreads, false><<<a.n_scenes, kThreads, 0, st>>>(a);
         break;
     case PH_SCATTER:
         if (a.audit & CERT_AUDIT_COST)
