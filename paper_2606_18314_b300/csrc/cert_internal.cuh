@@ -527,6 +527,14 @@ constexpr unsigned kFull = 0xffffffffu;
 // Lanes of a warp holding consecutive points form contiguous runs of equal
 // scene id (scenes are contiguous ranges).  Each helper reduces within the run
 // and lets the run's lowest lane issue one atomic.  s < 0 marks an idle lane.
+// Scene of point (or sorted slot) i.  A context of one scene needs no lookup,
+// so the loads that depend on the scene (its parameters and state) are not
+// held up behind one: a lone scene's steps are chains of dependent accesses.
+__device__ __forceinline__ int scene_of_point(const int32_t *scene_of, int n_scenes, int i)
+{
+    return n_scenes == 1 ? 0 : scene_of[i];
+}
+
 // Increment counter k of a per-bucket or per-entropy-cell count array and
 // return its previous value.  c16: the counts are 16-bit, two per word (every
 // scene has fewer than 65,536 points, so no count reaches 2^16 and the low

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_prepare(const StepArgs a)   // 
         s[k] = -1;
         p[k] = po[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < a.n_total) {
-            s[k] = a.scene_of[i];
+            s[k] = scene_of_point(a.scene_of, a.n_scenes, i);
             if (a.mode == MODE_REBUILD) {
                 p[k] = a.pos_new[i];
             } else {
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const StepArgs a)
         sc[k] = -1;
         hc[k] = 0;
         if (i < a.n_total) {
-            const int s = a.scene_of[i];
+            const int s = scene_of_point(a.scene_of, a.n_scenes, i);
             sc[k] = s;
             uint32_t r;
             f[k] = frontier_item<DIM>(a, i, s, eps_of(a.acc, s), &r);
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_refresh(const StepArgs a)
         na[k] = nb[k] = nc[k] = -1;
         Lold[k] = 0.0f;
         if (i < a.n_total) {
-            s[k] = a.scene_of[i];
+            s[k] = scene_of_point(a.scene_of, a.n_scenes, i);
             br[k] = a.brank[i];
             p[k] = a.pos_new[i];
             if (step) {
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
         const long long t0 = COST ? clock64() : 0;   // cost audit: this query's cycles
         if (active) {
             const int slot = s_list[e];
-            s = a.scene_of[slot];        // slot ranges of scenes equal their point ranges
+            s = scene_of_point(a.scene_of, a.n_scenes, slot);   // slot ranges of scenes equal their point ranges
             const SceneParams sp = a.sp[s];
             const SceneState &st = a.st[s];
             int gi = sorted_index(a.squad, slot - sp.pt_off + sp.s_off);
@@ -722,7 +722,7 @@ __device__ void far_items(const StepArgs &a, int first, int stride, float (*s_d)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int item = first; item < nfar; item += stride) {
         const int slot = a.far_list[item];
-        const int s = a.scene_of[slot];
+        const int s = scene_of_point(a.scene_of, a.n_scenes, slot);
         const SceneParams sp = a.sp[s];
         int gi = sorted_index(a.squad, slot - sp.pt_off + sp.s_off);
         if ((unsigned)(gi - sp.pt_off) >= (unsigned)sp.n) gi = slot;
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(kThreads) k_geometry(const StepArgs a)
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
     bool f = false;
     if (i < a.n_total) {
-        s = a.scene_of[i];
+        s = scene_of_point(a.scene_of, a.n_scenes, i);
         p = a.pos_new[i];
         f = a.failed[i] != 0;
     }
