@@ -576,12 +576,25 @@ __global__ void __launch_bounds__(kThreads, 4) k_search(const StepArgs a)   // 6
              : (PER == 2) ? (uint32_t)*reinterpret_cast<const uint16_t *>(a.sflag + base)
                           : (uint32_t)a.sflag[base];
     uint32_t count;
-    uint32_t pre = block_exclusive_scan(__popc(fw), &count, s_warp);
+    if constexpr (CHUNK <= 32) {
+        // a chunk of at most one warp's slots (small grids): warp 0 compacts it by
+        // a ballot, one barrier instead of a block scan's
+        __shared__ uint32_t s_count;
+        if (threadIdx.x < 32) {
+            const unsigned m = __ballot_sync(kFull, fw != 0u);
+            if (fw) s_list[__popc(m & ((1u << threadIdx.x) - 1u))] = base;
+            if (threadIdx.x == 0) s_count = (uint32_t)__popc(m);
+        }
+        __syncthreads();
+        count = s_count;
+    } else {
+        uint32_t pre = block_exclusive_scan(__popc(fw), &count, s_warp);
 #pragma unroll
-    for (int u = 0; u < PER; ++u)
-        if ((fw >> (8 * u)) & 0xffu) s_list[pre++] = base + u;
-    if (kOrdered && threadIdx.x == 0) a.chunk_cnt[chunk] = (int)count;   // the next step's order
-    __syncthreads();
+        for (int u = 0; u < PER; ++u)
+            if ((fw >> (8 * u)) & 0xffu) s_list[pre++] = base + u;
+        if (kOrdered && threadIdx.x == 0) a.chunk_cnt[chunk] = (int)count;   // the next step's order
+        __syncthreads();
+    }
 
     // G == 1: a warp searches a batch of 32 consecutive queries, then claims the
     // CTA's next unclaimed batch, so warps that drew short boxes take more
