@@ -152,6 +152,14 @@ __device__ int select_scene(const StepArgs &a, int s, float eps, int nF, double 
     static_assert(NT >= 256 && NT % 32 == 0, "the MLP layers use the first eight warps");
     const SceneParams sp = a.sp[s];
     const int ns = min(sp.n, kMedianSample);
+    // thread 0: the scene's state, read once here and written once at the end,
+    // and the frontier's entropy, whose table reads overlap the histograms
+    SceneState st;
+    double Hc = 0.0;
+    if (threadIdx.x == 0) {
+        st = a.st[s];
+        if (a.mode == MODE_STEP) Hc = norm_entropy(a.nlogn, nF, s_front, occ);
+    }
     for (int k = threadIdx.x; k < kTruncBins; k += NT) {
         sm.hc[k] = 0u;
         sm.hd[k] = 0u;
@@ -177,8 +185,6 @@ __device__ int select_scene(const StepArgs &a, int s, float eps, int nF, double 
         if (strat == STRAT_AUTO) strat = a.scene_policy ? a.scene_policy[s] : a.policy;
         // ---- the eight selector features of this step (stored every step)
         if (threadIdx.x == 0) {
-            const SceneState st = a.st[s];
-            const double Hc = norm_entropy(a.nlogn, nF, s_front, occ);
             float x[8];
             x[0] = (float)nF / (float)sp.n;                               // |F|/N
             x[1] = (float)Hc;                                             // H of the detected frontier
@@ -252,18 +258,15 @@ __device__ int select_scene(const StepArgs &a, int s, float eps, int nF, double 
             if (threadIdx.x == 0) {
                 const float pi = sm.out[0] + b3[0];
                 const float pr = sm.out[1] + b3[1];
-                SceneState st = a.st[s];
                 st.pred_inc = pi;
                 st.pred_reb = pr;
                 if (isfinite(pi) && isfinite(pr)) strat = (pi <= pr) ? STRAT_INC : STRAT_REB;
                 st.prev_pred_ratio = isfinite(pi - pr) ? (pi - pr) : 0.0f;
-                a.st[s] = st;
             }
             __syncthreads();
         }
     }
     if (threadIdx.x == 0) {
-        SceneState st = a.st[s];
         st.med_c = med_c;
         st.med_d2 = med_d2;
         int g = sp.g_default;
