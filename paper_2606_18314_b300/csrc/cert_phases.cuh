@@ -101,29 +101,48 @@ __device__ __forceinline__ double norm_entropy(const double *tab, int n, double 
 // block scan replace a full sort.  Values are non-negative (or +inf).
 constexpr int kTruncBins = 2048;
 
+// The two order statistics of select_scene in one pass: rank rc of the
+// histogram hc and rank rd of hd, from one block scan of both bin counts
+// packed into one word (each histogram holds at most kMedianSample <= 65,535
+// values, so the low half never carries into the high one).  Returns the two
+// truncated values in *vc and *vd (every thread).
 template <int NT>
-__device__ uint32_t trunc_select(const uint32_t *hist, int rank, uint32_t *s_warp, int *s_bin)
+__device__ void trunc_select2(const uint32_t *hc, const uint32_t *hd, int rc, int rd, uint32_t *s_warp,
+                              int *s_bin, uint32_t *vc, uint32_t *vd)
 {
     constexpr int per = kTruncBins / NT;
     static_assert(per >= 1 && kTruncBins % NT == 0, "bins split evenly over the block");
-    uint32_t sum = 0;
+    uint32_t sc = 0, sd = 0;
 #pragma unroll
-    for (int k = 0; k < per; ++k) sum += hist[threadIdx.x * per + k];
+    for (int k = 0; k < per; ++k) {
+        sc += hc[threadIdx.x * per + k];
+        sd += hd[threadIdx.x * per + k];
+    }
     uint32_t tot;
-    uint32_t pre = block_exclusive_scan<NT>(sum, &tot, s_warp);
-    if (pre <= (uint32_t)rank && (uint32_t)rank < pre + sum) {
+    const uint32_t pre = block_exclusive_scan<NT>(sc | (sd << 16), &tot, s_warp);
+    uint32_t pc = pre & 0xffffu, pd = pre >> 16;
+    if (pc <= (uint32_t)rc && (uint32_t)rc < pc + sc) {
         for (int k = 0; k < per; ++k) {
-            pre += hist[threadIdx.x * per + k];
-            if ((uint32_t)rank < pre) {
-                *s_bin = threadIdx.x * per + k;
+            pc += hc[threadIdx.x * per + k];
+            if ((uint32_t)rc < pc) {
+                s_bin[0] = threadIdx.x * per + k;
+                break;
+            }
+        }
+    }
+    if (pd <= (uint32_t)rd && (uint32_t)rd < pd + sd) {
+        for (int k = 0; k < per; ++k) {
+            pd += hd[threadIdx.x * per + k];
+            if ((uint32_t)rd < pd) {
+                s_bin[1] = threadIdx.x * per + k;
                 break;
             }
         }
     }
     __syncthreads();
-    const uint32_t bin = (uint32_t)*s_bin;
+    *vc = (uint32_t)s_bin[0] << 20;
+    *vd = (uint32_t)s_bin[1] << 20;
     __syncthreads();
-    return bin << 20;
 }
 
 // Shared memory of select_scene.
@@ -131,7 +150,7 @@ struct SelectSmem {
     uint32_t hc[kTruncBins];
     uint32_t hd[kTruncBins];
     uint32_t warp[32];
-    int bin;
+    int bins[2];
     float feat[8];
     __align__(16) float h1[64];
     __align__(16) float h2[64];
@@ -175,9 +194,11 @@ __device__ int select_scene(const StepArgs &a, int s, float eps, int nF, double 
     }
     __syncthreads();
     // lower median of the clearances; the cell-size reference quantile of d2
-    const float med_c = __uint_as_float(trunc_select<NT>(sm.hc, (ns - 1) / 2, sm.warp, &sm.bin));
     const int qi = min(ns - 1, max(0, (int)(a.cell_quantile * (float)(ns - 1))));
-    const float med_d2 = __uint_as_float(trunc_select<NT>(sm.hd, qi, sm.warp, &sm.bin));
+    uint32_t vc, vd;
+    trunc_select2<NT>(sm.hc, sm.hd, (ns - 1) / 2, qi, sm.warp, sm.bins, &vc, &vd);
+    const float med_c = __uint_as_float(vc);
+    const float med_d2 = __uint_as_float(vd);
 
     int strat = STRAT_INC;
     if (a.mode == MODE_STEP) {
